@@ -1,0 +1,37 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+Holds no arithmetic of the method: only a counter-based uniform generator.
+SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) is applied to ``seed XOR index``; the top 53 bits
+of the mixed word give a uniform double in [0, 1), mapped to [-1, 1).  The
+index of a state entry is its canonical position (k*Np + j)*Q + i, so the
+draw does not depend on any internal layout.  The CUDA library implements
+the same published generator in its own code for ``fedbm_set_equilibrium``.
+"""
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(x):
+    """One SplitMix64 output for each uint64 state value in x."""
+    z = np.asarray(x, dtype=np.uint64) + _GAMMA
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def uniform_pm1(seed, n, start=0):
+    """n doubles in [-1, 1) for canonical indices start .. start+n-1."""
+    idx = np.arange(start, start + n, dtype=np.uint64)
+    z = splitmix64(np.uint64(seed) ^ idx)
+    u01 = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return 2.0 * u01 - 1.0
+
+
+def perturbation(seed, K, Np, Q):
+    """Uniform [-1, 1) field of shape [K, Np, Q] (canonical layout)."""
+    with np.errstate(over="ignore"):
+        return uniform_pm1(seed, K * Np * Q).reshape(K, Np, Q)

@@ -1,0 +1,206 @@
+"""Pins of the oracle's residual, walls and time marching (Sec. II, III)."""
+import numpy as np
+import pytest
+
+from oracle import couette, dg, velset
+from paper_2012_13487_gb300 import inputs
+
+
+def _random_state(pr, seed=7, amp=0.3):
+    u = inputs.perturbation(seed, pr.K, pr.Np, pr.Q)
+    return pr.equilibrium_state(1.0, 0.02, -0.01, amp, u)
+
+
+@pytest.mark.parametrize("vs,order", [(("gh", 4), 2), (("gh", 4), 3), (("nc", 16), 2), (("gh", 6), 3)])
+def test_collision_conserves_mass_and_momentum(vs, order):
+    ex, ey, w = velset.velocity_set(*vs)
+    rng = np.random.default_rng(3)
+    f = w * (1.0 + 0.4 * rng.uniform(-1, 1, size=(50, len(w))))
+    rho, ux, uy = dg.moments(f, ex, ey)
+    feq = dg.equilibrium(rho, ux, uy, ex, ey, w, order)
+    d = feq - f
+    assert np.abs(d.sum(-1)).max() < 1e-15 * 10
+    assert np.abs(d @ ex).max() < 1e-14
+    assert np.abs(d @ ey).max() < 1e-14
+
+
+def test_equilibrium_low_mach_expansion_of_maxwellian():
+    # for small u the Hermite f^eq approaches the discrete Maxwellian ratio
+    ex, ey, w = velset.velocity_set("gh", 6)
+    u = (1e-3, -2e-3)
+    maxw = w * np.exp(ex * u[0] + ey * u[1] - 0.5 * (u[0] ** 2 + u[1] ** 2))
+    for order, tol in ((2, 1e-8), (3, 1e-11)):
+        feq = dg.equilibrium(1.0, u[0], u[1], ex, ey, w, order)
+        assert np.abs(feq - maxw).max() / w.max() < tol
+
+
+def test_tau_from_kn():
+    assert dg.tau_from_kn(1.0) == pytest.approx(1 / np.sqrt(3), rel=1e-15)
+    assert dg.tau_from_kn(8.0, L=2.0) == pytest.approx(16 / np.sqrt(3), rel=1e-15)
+
+
+def test_free_stream_periodic_is_steady():
+    pr = dg.Problem(4, 3, 3, velset=("gh", 4), eq_order=3, bc=("periodic",) * 4)
+    f = pr.equilibrium_state(1.1, 0.05, -0.03)
+    assert np.abs(pr.rhs(f)).max() < 1e-13
+
+
+@pytest.mark.parametrize("wall", ["diffuse", "eq"])
+def test_rest_state_with_resting_walls_is_steady(wall):
+    pr = dg.Problem(3, 3, 2, velset=("nc", 8), bc=(wall,) * 4, wall_u=((0, 0),) * 4)
+    f = pr.equilibrium_state()
+    assert np.abs(pr.rhs(f)).max() < 1e-13
+
+
+def test_diffuse_walls_conserve_mass_eq_walls_do_not():
+    for bc, conserves in ((("diffuse",) * 4, True), (("eq",) * 4, False)):
+        pr = dg.Problem(3, 3, 2, velset=("gh", 4), bc=bc,
+                        wall_u=((0, 0), (0, 0), (0.1, 0), (0, 0)))
+        f = _random_state(pr)
+        dmass = np.sum(pr.geo["J"][:, None] * (pr.rhs(f).sum(-1) @ pr.ops.M))
+        if conserves:
+            assert abs(dmass) < 1e-14
+        else:
+            assert abs(dmass) > 1e-6
+
+
+def test_mass_conserved_over_lsrk_steps_cavity():
+    pr = dg.Problem(4, 4, 2, velset=("gh", 4), bc=("diffuse",) * 4,
+                    wall_u=((0, 0), (0, 0), (0.1, 0), (0, 0)))
+    f = _random_state(pr, amp=1e-3)
+    m0 = pr.mass(f)
+    f = pr.run(f, 20)
+    assert abs(pr.mass(f) - m0) < 1e-14
+
+
+def test_p0_is_first_order_upwind_finite_volume():
+    pr = dg.Problem(3, 2, 0, velset=("gh", 2), bc=("periodic",) * 4)
+    f = _random_state(pr)
+    got = pr.rhs(f)[:, 0, :]
+    K, Q = pr.K, pr.Q
+    want = np.zeros((K, Q))
+    area = 0.5 * (1 / 3) * (1 / 2)
+    rho, ux, uy = dg.moments(f[:, 0, :], pr.ex, pr.ey)
+    feq = dg.equilibrium(rho, ux, uy, pr.ex, pr.ey, pr.w)
+    for k in range(K):
+        for i in range(Q):
+            acc = 0.0
+            for fc in range(3):
+                a, b = fc, (fc + 1) % 3
+                dx = pr.vx[k, b] - pr.vx[k, a]
+                dy = pr.vy[k, b] - pr.vy[k, a]
+                length = np.hypot(dx, dy)
+                en = (pr.ex[i] * dy - pr.ey[i] * dx) / length
+                fup = f[k, 0, i] if en > 0 else f[pr.nbr_elem[k, fc], 0, i]
+                acc -= length * en * fup
+            want[k, i] = acc / area - (f[k, 0, i] - feq[k, i]) / pr.tau
+    np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_advection_translates_at_order_p_plus_1():
+    def g(x, y):
+        return 1.0 + 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+
+    errs = []
+    T = 0.05
+    for N in (8, 16):          # N = 4 is still pre-asymptotic in the max norm
+        pr = dg.Problem(N, N, 2, velset=("gh", 2), bc=("periodic",) * 4, collision=False, cfl=0.25)
+        nsteps = int(np.ceil(T / pr.dt))
+        pr.dt = T / nsteps
+        f = pr.w[None, None, :] * g(pr.x, pr.y)[:, :, None]
+        f = pr.run(f, nsteps)
+        exact = pr.w[None, None, :] * g(pr.x[:, :, None] - pr.ex * T, pr.y[:, :, None] - pr.ey * T)
+        errs.append(np.abs(f - exact).max())
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > 2.6, (errs, rate)
+
+
+def test_central_flux_is_energy_neutral_upwind_dissipates():
+    # (1/2) d/dt sum_k J f^T M f: zero for central flux, negative for upwind
+    for beta, sign in ((0.5, 0), (1.0, -1)):
+        pr = dg.Problem(3, 3, 2, velset=("gh", 2), bc=("periodic",) * 4, collision=False, beta=beta)
+        f = _random_state(pr, amp=0.5)
+        dfdt = pr.rhs(f)
+        rate = sum(pr.geo["J"][k] * np.einsum("nq,nm,mq->", f[k], pr.ops.M, dfdt[k]) for k in range(pr.K))
+        if sign == 0:
+            assert abs(rate) < 1e-13
+        else:
+            assert rate < -1e-6
+
+
+def _butcher_from_2n():
+    A, B = dg.LSRK_A, dg.LSRK_B
+    s = 5
+    a = np.zeros((s, s))
+    b = np.zeros(s)
+    du = np.zeros(s)
+    u = np.zeros(s)
+    for st in range(s):
+        a[st] = u                # stage st evaluates L at the current u
+        du = A[st] * du
+        du[st] += 1.0
+        u = u + B[st] * du
+    b = u
+    return a, b
+
+
+def test_lsrk_order_conditions():
+    a, b = _butcher_from_2n()
+    c = a.sum(1)
+    np.testing.assert_allclose(c, dg.LSRK_C, atol=1e-15)
+    conds = [(b.sum(), 1), (b @ c, 1 / 2), (b @ c ** 2, 1 / 3), (b @ a @ c, 1 / 6),
+             (b @ c ** 3, 1 / 4), (b @ (c * (a @ c)), 1 / 8), (b @ a @ c ** 2, 1 / 12),
+             (b @ a @ a @ c, 1 / 24)]
+    for got, want in conds:
+        assert abs(got - want) < 1e-15
+
+
+def test_lsrk_fourth_order_in_time():
+    lam = -1.0 + 2.0j
+    errs = []
+    for n in (20, 40):
+        dt = 1.0 / n
+        y, res = 1.0 + 0j, 0j
+        for _ in range(n):
+            for s in range(5):
+                res = dg.LSRK_A[s] * res + dt * lam * y
+                y = y + dg.LSRK_B[s] * res
+        errs.append(abs(y - np.exp(lam)))
+    assert 3.8 < np.log2(errs[0] / errs[1]) < 4.3
+
+
+def test_couette_closed_form_matches_linearized_solve_and_tau_reading():
+    y = np.linspace(0, 1, 9)
+    for kn in (0.25, 1.0, 1.5):
+        a = couette.exact_ux(y, kn, 0.1, -0.1)
+        b = couette.linearized_steady(y, dg.tau_from_kn(kn), 0.1, -0.1)
+        assert np.abs(a - b).max() < 1e-12
+    # the other typesetting reading of eq. KnTau (tau = Kn sqrt3) is far off
+    b = couette.linearized_steady(y, np.sqrt(3.0), 0.1, -0.1)
+    assert np.abs(couette.exact_ux(y, 1.0, 0.1, -0.1) - b).max() > 1e-2
+    assert couette.exact_ux(1.0, 1.0, 0.1, -0.1) == pytest.approx(0.0510300760, abs=1e-10)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_couette_steady_state_converges_at_p_plus_1(p):
+    Uw = 1e-3
+    errs = []
+    for Ny in (2, 4, 8):
+        pr = dg.Problem(1, Ny, p, velset=("gh", 4), kn=1.0,
+                        wall_u=((-Uw, 0), (0, 0), (Uw, 0), (0, 0)))
+        f0 = pr.equilibrium_state()
+        f, res = dg.steady_state(pr, f0)
+        assert res < 1e-12
+        assert abs(pr.mass(f) - pr.mass(f0)) < 1e-10
+        _, ux, _ = pr.nodal_moments(f)
+        errs.append(pr.l2_error(ux, lambda x, yy: couette.exact_ux(yy, 1.0, Uw, -Uw)) / (2 * Uw))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > p + 1 - 0.15), rates
+    assert errs[-1] < (1e-4 if p == 1 else 1e-6)
+
+
+def test_splitmix64_reference_output():
+    # first output of SplitMix64 seeded with 0 (published reference value)
+    assert int(inputs.splitmix64(np.array([0], dtype=np.uint64))[0]) == 0xE220A8397B1DCDAF
+    u = inputs.uniform_pm1(5, 10000)
+    assert u.min() >= -1 and u.max() < 1 and abs(u.mean()) < 0.05
