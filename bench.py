@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused DG-FEM discrete-velocity BGK stage.
+
+One "step" is one full LSRK(5,4) time step (five fused stage kernels) of the
+whole mesh.  The metric is DOF-stage updates per second:
+K * Np * Q * 5 * steps / time, a DOF being one (element, node, velocity) value.
+
+Default workload: lid-driven cavity at Kn = 1 on a 64x64x2 triangle mesh,
+p = 4 (15 nodes), 16x16 Newton-Cotes velocities on [-4, 4] sqrt(RT), lid
+speed 0.1 sqrt(RT), diffuse walls, FP32, rest-equilibrium start (31.5M DOF;
+the two state buffers and the residual, 378 MB, are larger than L2, so no L2
+flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Under torchrun each rank runs an independent replica of the workload (the
+solver needs no communication); the value is the sum over ranks of the
+DOF-stage updates divided by the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cavity_kn1_64x64x2_p4_nc16x16_fp32": dict(
+        kind="cavity", nx=64, ny=64, p=4, vel=("nc", 16), kn=1.0, speed=0.1, precision="fp32",
+        desc="lid-driven cavity Kn=1, 64x64x2 triangles, p=4, NC 16x16 on [-4,4]sqrt(RT), lid 0.1, FP32"),
+    "cavity_kn1_64x64x2_p4_gh16_fp32": dict(
+        kind="cavity", nx=64, ny=64, p=4, vel=("gh", 4), kn=1.0, speed=0.1, precision="fp32",
+        desc="lid-driven cavity Kn=1, 64x64x2 triangles, p=4, GH D2Q16, lid 0.1, FP32"),
+    "couette_kn1_256x256x2_p5_gh16_fp32": dict(
+        kind="couette", nx=256, ny=256, p=5, vel=("gh", 4), kn=1.0, speed=0.1, precision="fp32",
+        desc="Couette Kn=1, 256x256x2 triangles, p=5, GH D2Q16, walls -+0.1, FP32"),
+    "couette_kn1_256x256x2_p5_gh16_bf16": dict(
+        kind="couette", nx=256, ny=256, p=5, vel=("gh", 4), kn=1.0, speed=0.1, precision="bf16",
+        desc="Couette Kn=1, 256x256x2 triangles, p=5, GH D2Q16, walls -+0.1, BF16 deviation state"),
+    "cavity_kn8_128x128x2_p3_nc32x32_bf16": dict(
+        kind="cavity", nx=128, ny=128, p=3, vel=("nc", 32), kn=8.0, speed=0.1, precision="bf16",
+        desc="lid-driven cavity Kn=8, 128x128x2 triangles, p=3, NC 32x32, BF16 deviation state, FP64 moments",
+        reduction="fp64"),
+}
+DEFAULT_WORKLOAD = "cavity_kn1_64x64x2_p4_nc16x16_fp32"
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
+RED = {"default": 0, "fp64": 1, "comp": 2}
+# algorithmic bytes per DOF for one stage: f read + res read + res write + f write
+STATE_BYTES = {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2}
+RES_BYTES = {"fp64": 8, "fp32": 4, "bf16": 4, "fp16": 4}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def algorithmic_bytes_per_dof_step(prec):
+    """Five stages; the first has A = 0 and does not read the residual."""
+    s, r = STATE_BYTES[prec], RES_BYTES[prec]
+    return (2 * s + r) + 4 * (2 * s + 2 * r)
+
+
+def dims(w):
+    p = w["p"]
+    Np = (p + 1) * (p + 2) // 2
+    Q = w["vel"][1] ** 2
+    K = 2 * w["nx"] * w["ny"]
+    return K, Np, Q
+
+
+def stage_kernel_sha():
+    h = hashlib.sha256()
+    for n in ("stage_impl.cuh", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2012_13487_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was
+    taken for the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_%s.md" % name)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m1 = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m1 or not m2 or m1.group(1) != stage_kernel_sha():
+        return None
+    return float(m2.group(1))
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if key in d:
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_median": statistics.median(float(r[3]) for r in rows
+                                                    if r[3].replace(".", "").isdigit()) if rows else None}
+
+
+def make_solver(w, stream_handle):
+    from paper_2012_13487_gb300 import fedbm as fb
+    if w["kind"] == "cavity":
+        bc = (fb.BC_WALL_DIFFUSE,) * 4
+        wall = ((0, 0), (0, 0), (w["speed"], 0), (0, 0))
+    else:
+        bc = (fb.BC_WALL_DIFFUSE, fb.BC_PERIODIC, fb.BC_WALL_DIFFUSE, fb.BC_PERIODIC)
+        wall = ((-w["speed"], 0), (0, 0), (w["speed"], 0), (0, 0))
+    m = fb.mesh_desc(w["nx"], w["ny"], w["p"], bc=bc, wall_u=wall)
+    kind, n = w["vel"]
+    v = fb.velset_desc(fb.VELSET_GH if kind == "gh" else fb.VELSET_NC, n, eq_order=w.get("eq_order", 2))
+    prm = fb.params(kn=w["kn"], precision=PREC[w["precision"]], reduction=RED[w.get("reduction", "default")],
+                    cfl=0.5)
+    return fb.Solver(m, v, prm, stream_handle)
+
+
+# ---------------------------------------------------------------- oracle timing
+ORACLE_SAMPLE_SCRIPT = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle import dg
+from paper_2012_13487_gb300 import inputs
+w = json.loads(%(w)r)
+kind, n = w["vel"]
+if w["kind"] == "cavity":
+    bc = ("diffuse",) * 4; wall = ((0, 0), (0, 0), (w["speed"], 0), (0, 0))
+else:
+    bc = ("diffuse", "periodic", "diffuse", "periodic"); wall = ((-w["speed"], 0), (0, 0), (w["speed"], 0), (0, 0))
+pr = dg.Problem(w["nx"], w["ny"], w["p"], velset=(kind, n), kn=w["kn"], bc=bc, wall_u=wall)
+f0 = pr.equilibrium_state(amp=1e-3, u=inputs.perturbation(1, pr.K, pr.Np, pr.Q))
+rng = np.random.default_rng(0)
+elems = np.sort(rng.choice(pr.K, min(pr.K, %(nelem)d), replace=False))
+res = np.zeros((len(elems), pr.Np, pr.Q))
+t_end = time.perf_counter() + %(seconds)f
+stages = 0
+t0 = time.perf_counter()
+while stages < %(min_stages)d or time.perf_counter() < t_end:
+    f1, res = pr.lsrk_stage(1, f0, res, elems)
+    stages += 1
+    if stages >= %(max_stages)d:
+        break
+dt = time.perf_counter() - t0
+print(json.dumps({"dof_stages": stages * len(elems) * pr.Np * pr.Q, "seconds": dt, "stages": stages,
+                  "elements": int(len(elems)), "K": int(pr.K)}))
+"""
+
+
+def oracle_sample(w, seconds, nelem=512, min_stages=1, max_stages=10 ** 9):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    script = ORACLE_SAMPLE_SCRIPT % dict(root=ROOT, w=json.dumps(w), seconds=seconds, nelem=nelem,
+                                         min_stages=min_stages, max_stages=max_stages)
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------- arms
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, w, name):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    K, Np, Q = dims(w)
+    # each step: one LSRK stage of the oracle on 64 sampled elements (FP64)
+    totals, seconds = 0, 0.0
+    out = oracle_sample(w, seconds=0.0, nelem=64, min_stages=args.steps + args.warmup,
+                        max_stages=args.steps + args.warmup)
+    per_stage_s = out["seconds"] / out["stages"]
+    dof_per_stage = out["dof_stages"] / out["stages"]
+    value = dof_per_stage / per_stage_s
+    line = {
+        "impl": "reference", "metric": "DOF-stage updates/s", "value": value, "unit": "DOF-stage/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_stage_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "name": name, "K": K, "Np": Np, "Q": Q},
+        "cpu_baseline": {"value": value, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
+                         "sample": "FP64 NumPy oracle, one LSRK stage per step on 64 sampled elements "
+                                   "(%d DOF) of the %d-element mesh, single thread" % (dof_per_stage, K)},
+        "e2e": {"value": value, "unit": "DOF-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, w, name):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    st = torch.cuda.Stream()
+    K, Np, Q = dims(w)
+    dof = K * Np * Q
+    s = make_solver(w, st.cuda_stream)
+    s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.step(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    mass = s.mass()   # also raises on NaN / rho <= 0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    secs = ms / 1e3
+    value = world * dof * 5 * args.steps / secs
+
+    # roofline of the stage kernel: algorithmic bytes / average launch time
+    alg_bytes_step = dof * algorithmic_bytes_per_dof_step(w["precision"])
+    achieved = alg_bytes_step * args.steps / secs / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = recorded_traffic(name)
+
+    # end to end through the C ABI with host buffers
+    e2e_steps = max(3, min(args.steps, 20))
+    f_host = torch.empty((K, Np, Q), dtype=torch.float64).pin_memory()
+    s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+    from paper_2012_13487_gb300 import fedbm as fb
+    fb.fedbm_get_state(s.h, f_host, False)
+    rho = torch.empty((K, Np), dtype=torch.float64).pin_memory()
+    ux = torch.empty_like(rho).pin_memory()
+    uy = torch.empty_like(rho).pin_memory()
+    for _ in range(2):
+        fb.fedbm_set_state(s.h, f_host, False)
+        fb.fedbm_rk_step(s.h, 1)
+        fb.fedbm_get_moments(s.h, rho, ux, uy, False)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fb.fedbm_set_state(s.h, f_host, False)
+        fb.fedbm_rk_step(s.h, 1)
+        fb.fedbm_get_moments(s.h, rho, ux, uy, False)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * dof * 5 * e2e_steps / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out = oracle_sample(w, seconds=args.cpu_seconds)
+        cpu = {"value": out["dof_stages"] / out["seconds"], "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
+               "sample": "FP64 NumPy oracle, %d LSRK stages on %d sampled elements (%d DOF each) of the "
+                         "%d-element mesh, single thread, %.1f s" % (out["stages"], out["elements"],
+                                                                     out["dof_stages"] // out["stages"],
+                                                                     out["K"], out["seconds"])}
+    if rank == 0:
+        line = {
+            "metric": "DOF-stage updates/s", "value": value, "unit": "DOF-stage/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-state/f32", "fp16": "f16-state/f32"}[w["precision"]],
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "name": name, "K": K, "Np": Np, "Q": Q, "dof": dof,
+                       "l2": "inputs larger than L2 (state x2 + residual = %.0f MB), no flush" %
+                             (dof * (2 * STATE_BYTES[w["precision"]] + RES_BYTES[w["precision"]]) / 1e6),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_dof_step": algorithmic_bytes_per_dof_step(w["precision"]),
+                         "kernel": "stage_kernel (5 launches per step; average over the mix)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "DOF-stage/s", "steps": e2e_steps,
+                    "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": 3 * K * Np * 8,
+                    "path": "fedbm_set_state(host FP64) + fedbm_rk_step(1) + fedbm_get_moments(host)"},
+            "gpu_launches": 5 * args.steps,
+            "clocks": clocks,
+            "mass_after": mass,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w, args.workload)
+    else:
+        run_ours(args, w, args.workload)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * fedbm.h -- C ABI of the GB300 finite element discrete Boltzmann library.
+ *
+ * The library advances the discrete-velocity BGK equation
+ *     d f_i/dt + e_i . grad f_i = -(f_i - f_i^eq)/tau           (Sec. II.A, eq. DBE)
+ * discretised by nodal DG on straight-sided triangles (Sec. II.B.1, eq. byparts)
+ * with an upwind (or central) numerical flux, diffuse-scattering walls
+ * (Sec. II.A.4, eq. FullBC / eq. UsedBC), the Hermite equilibrium of eq. feq
+ * (optionally with the third Hermite term of eq. Herm3a), tau from eq. KnTau, and
+ * explicit five-stage fourth-order low-storage Runge-Kutta time marching (the
+ * paper's Sec. IV allows explicit RK of any order).  Every stage is one fused
+ * CUDA kernel on sm_103a.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: FEDBM_OK (0) on success, a negative FEDBM_E* code on error;
+ *    fedbm_last_error() then returns a message (thread-local storage, valid
+ *    until the next failing call on the same thread).  No C++ exception crosses
+ *    the ABI.
+ *  - Canonical state layout: double f[K][Np][Q], velocity index fastest.
+ *    Element k = 2*(iy*nx + ix) + t of square (ix, iy); t = 0 is the triangle
+ *    (A, B, C), t = 1 is (A, C, D), where A, B, C, D are the square's corners
+ *    (x0,y0), (x1,y0), (x1,y1), (x0,y1); nodes are the warp & blend nodes
+ *    (alpha = 0) numbered row by row in the reference s direction; velocity
+ *    i = ix*n + iy of the n x n tensor set.  Node moments use [K][Np].
+ *  - Ownership: the caller owns every buffer it passes; the library never keeps
+ *    a caller pointer after a call returns.  The library owns its device state
+ *    (allocated in fedbm_create, freed in fedbm_destroy) on the device that is
+ *    current when fedbm_create is called.
+ *  - Streams: all device work of a solver is ordered on the stream given to
+ *    fedbm_create (NULL = legacy default stream).  Calls marked "synchronous"
+ *    wait for that stream before returning.
+ *  - on_device = 1 means the pointer is device memory of the solver's device;
+ *    0 means host memory (pinned or pageable).
+ */
+#ifndef FEDBM_H
+#define FEDBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define FEDBM_OK          0
+#define FEDBM_EINVAL     -1   /* bad argument or descriptor                   */
+#define FEDBM_ENOMEM     -2   /* device or host allocation failed             */
+#define FEDBM_ECUDA      -3   /* a CUDA runtime call failed                   */
+#define FEDBM_ENONFINITE -4   /* NaN/Inf in the state or rho <= 0 at a node   */
+#define FEDBM_ETIMEOUT   -5   /* a bounded device-side wait gave up           */
+#define FEDBM_ENOTSUP    -6   /* configuration not compiled into the library  */
+
+/* ---- enumerations ------------------------------------------------------- */
+enum fedbm_bc_kind {
+  FEDBM_BC_PERIODIC     = 0,  /* pairs with the opposite side                 */
+  FEDBM_BC_WALL_DIFFUSE = 1,  /* eq. FullBC, zero net mass flux               */
+  FEDBM_BC_WALL_EQ      = 2   /* eq. UsedBC with rho_b = 1                    */
+};
+enum fedbm_velset_kind { FEDBM_VELSET_GH = 0, FEDBM_VELSET_NC = 1 };
+enum fedbm_precision {
+  FEDBM_FP64     = 0,         /* state, residual and arithmetic in FP64       */
+  FEDBM_FP32     = 1,         /* state, residual and arithmetic in FP32       */
+  FEDBM_BF16_DEV = 2,         /* state: BF16 per-element-scaled deviation from
+                                 the rest equilibrium; FP32 residual and math */
+  FEDBM_FP16_DEV = 3          /* same with FP16 deviation codes               */
+};
+enum fedbm_reduction {
+  FEDBM_RED_DEFAULT   = 0,    /* the compute precision (FP64 in FP64 mode,
+                                 FP32 otherwise)                              */
+  FEDBM_RED_FP64      = 1,    /* velocity moments accumulated in FP64          */
+  FEDBM_RED_COMP_FP32 = 2     /* compensated (Neumaier) FP32 accumulation      */
+};
+
+/* ---- descriptors -------------------------------------------------------- */
+/* Structured mesh on [0, lx] x [0, ly] (Sec. III: Cartesian cells split into two
+ * triangles).  Sides: 0 -> y = 0, 1 -> x = lx, 2 -> y = ly, 3 -> x = 0.
+ * Periodic sides must come in opposite pairs.  Wall velocities are tangential
+ * (the component normal to the wall must be 0). */
+typedef struct fedbm_mesh_desc {
+  int32_t nx, ny;        /* cells in x and y; K = 2 nx ny elements           */
+  int32_t order;         /* polynomial degree p, 0..6                         */
+  int32_t bc[4];         /* enum fedbm_bc_kind per side                        */
+  double  wall_ux[4];    /* wall velocity per side, units of sqrt(RT)          */
+  double  wall_uy[4];
+  double  lx, ly;        /* domain size; 0 means 1                              */
+} fedbm_mesh_desc;
+
+/* Velocity set (Sec. II.A.3, Table 1; Newton-Cotes grid of Sec. III.B).
+ * Velocities are in units of sqrt(RT) (theta = RT = c_s^2 = 1); Q = n * n. */
+typedef struct fedbm_velset_desc {
+  int32_t kind;          /* enum fedbm_velset_kind                              */
+  int32_t n;             /* 1-D points (GH: 1..40, NC: 2..64)                   */
+  double  nc_extent;     /* NC nodes on [-extent, extent] (0 means 4)           */
+  int32_t nc_sqrt2;      /* NC grid unit: 0 -> sqrt(RT), 1 -> sqrt(2RT)         */
+  int32_t eq_order;      /* Hermite order of f^eq: 2 (eq. feq) or 3 (eq. Herm3a) */
+} fedbm_velset_desc;
+
+typedef struct fedbm_params {
+  double  kn;            /* Knudsen number; tau = kn*length/sqrt(3) (eq. KnTau) */
+  double  length;        /* characteristic length L (0 means 1)                 */
+  double  beta;          /* flux parameter: 1 upwind, 0.5 central (Sec. II.B.1) */
+  double  cfl;           /* dt = cfl*r_in,min/(max|e|*(p+1)^2) when dt <= 0     */
+  double  dt;            /* explicit time step (> 0 overrides cfl)              */
+  int32_t precision;     /* enum fedbm_precision                                */
+  int32_t reduction;     /* enum fedbm_reduction                                */
+  int32_t collision;     /* 1: BGK collision on; 0: pure advection              */
+  int32_t elems_per_cta; /* stage-kernel tile: elements per CTA (0 = auto)      */
+  int32_t threads_per_cta; /* stage-kernel tile: threads per CTA (0 = auto)     */
+} fedbm_params;
+
+typedef struct fedbm_info_t {
+  int64_t K, Np, Nfp, Q, Q_padded;
+  double  dt, tau, time;
+  int64_t steps;                 /* completed RK steps                           */
+  int32_t precision, reduction, order, eq_order;
+  int32_t elems_per_cta, threads_per_cta;
+  int64_t state_bytes;           /* device bytes of one state buffer             */
+  int64_t residual_bytes;        /* device bytes of the RK residual              */
+} fedbm_info_t;
+
+typedef struct fedbm_solver fedbm_solver;   /* opaque, library-owned */
+
+/* ---- host-only queries (no GPU needed) ---------------------------------- */
+
+/* 2-D velocity set of a descriptor (Sec. II.A.3, Table 1).  Writes Q values to
+ * each of ex, ey, w (any may be NULL) and Q to *q.  Pass ex = ey = w = NULL to
+ * query Q first.  Errors: EINVAL for an unsupported descriptor. */
+int fedbm_velset(const fedbm_velset_desc* vs, double* ex, double* ey, double* w, int32_t* q);
+
+/* Reference-element operators of degree p (Sec. II.B.1): nodes r, s [Np];
+ * derivative matrices Dr, Ds [Np][Np] row-major; LIFT [Np][3*Nfp] (inverse
+ * mass matrix times the face mass matrices, faces 0: s=-1, 1: r+s=0, 2: r=-1,
+ * face nodes in increasing r, s, s); mass matrix M [Np][Np]; fmask [3][Nfp].
+ * Any output may be NULL.  Errors: EINVAL if p is outside 0..6. */
+int fedbm_ref_operators(int32_t p, double* r, double* s, double* Dr, double* Ds,
+                        double* LIFT, double* M, int32_t* fmask);
+
+/* Physical node coordinates x, y [K][Np] of a mesh descriptor, and the time
+ * step the given velocity set / params would use (*dt, may be NULL). */
+int fedbm_mesh_nodes(const fedbm_mesh_desc* mesh, const fedbm_velset_desc* vs,
+                     const fedbm_params* prm, double* x, double* y, double* dt);
+
+/* Face connectivity of a mesh descriptor: nbr[K][3].  For face f of element k
+ * (face f joins vertices f and f+1 mod 3 of the counter-clockwise triangle),
+ * nbr = (kn << 3) | (fn << 1) | rev with kn the neighbour element, fn its face
+ * and rev = 1 when the two faces list their shared nodes in opposite order; a
+ * wall face stores -(side + 1).  Periodic sides wrap to the opposite side. */
+int fedbm_mesh_connectivity(const fedbm_mesh_desc* mesh, int32_t* nbr);
+
+/* ---- solver lifecycle ---------------------------------------------------- */
+
+/* Build the velocity set, mesh, operators and wall data on the host in FP64,
+ * upload them, and allocate the device state (two state buffers and one
+ * residual).  cuda_stream is a cudaStream_t (NULL = default stream).  The
+ * state is left zero; call fedbm_set_state or fedbm_set_equilibrium before
+ * stepping.  Errors: EINVAL, ENOMEM, ECUDA, ENOTSUP. */
+int fedbm_create(const fedbm_mesh_desc* mesh, const fedbm_velset_desc* vs,
+                 const fedbm_params* prm, void* cuda_stream, fedbm_solver** out);
+
+/* Free every device and host resource of the solver (NULL is allowed). */
+void fedbm_destroy(fedbm_solver* s);
+
+/* Load a canonical FP64 state f[K][Np][Q] (host or device) and encode it into
+ * the storage precision.  Resets time and step count to 0.  Asynchronous for
+ * device input; host input is copied before the call returns. */
+int fedbm_set_state(fedbm_solver* s, const double* f, int32_t on_device);
+
+/* f_i = f_i^eq(rho0, u0) * (1 + amp * u), u in [-1, 1) drawn by SplitMix64 at
+ * canonical index (k*Np + j)*Q + i of seed (a seeded perturbation of an
+ * equilibrium, computed on the device).  Resets time and step count. */
+int fedbm_set_equilibrium(fedbm_solver* s, double rho0, double ux0, double uy0,
+                          double amp, uint64_t seed);
+
+/* Advance nsteps full LSRK(5,4) steps (5 fused stage kernels each), replayed
+ * from a CUDA graph captured on first use.  Asynchronous. */
+int fedbm_rk_step(fedbm_solver* s, int32_t nsteps);
+
+/* Run one LSRK(5,4) stage (0..4) with the same kernel rk_step uses; stage 0
+ * ignores the residual's previous contents (its A coefficient is 0).  For
+ * testing single stages.  Asynchronous. */
+int fedbm_rk_stage(fedbm_solver* s, int32_t stage);
+
+/* Node moments rho, u_x, u_y [K][Np] in FP64 of the current state.
+ * Synchronous for host outputs. */
+int fedbm_get_moments(fedbm_solver* s, double* rho, double* ux, double* uy, int32_t on_device);
+
+/* Decode the current state into canonical FP64 f[K][Np][Q].  Synchronous for
+ * host output. */
+int fedbm_get_state(fedbm_solver* s, double* f, int32_t on_device);
+
+/* Decode the LSRK residual register into canonical FP64 [K][Np][Q]. */
+int fedbm_get_residual(fedbm_solver* s, double* res, int32_t on_device);
+
+/* Global mass sum_k J_k 1^T M rho_k accumulated in FP64 (synchronous).
+ * Returns ENONFINITE if any node has a non-finite value or rho <= 0, and
+ * ETIMEOUT if a stage kernel reported a bounded wait that gave up. */
+int fedbm_mass(fedbm_solver* s, double* total_mass);
+
+int fedbm_info(const fedbm_solver* s, fedbm_info_t* info);
+
+const char* fedbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEDBM_H */

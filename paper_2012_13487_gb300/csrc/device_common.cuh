@@ -1,0 +1,101 @@
+// Shared device-side definitions of the fused LSRK stage kernel.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fedbm {
+
+// Storage forms of the distribution state.  Plain forms store f itself; the
+// deviation forms store q with f_i = w_i (1 + s_k q_i), s_k a per-element
+// power-of-two scale, and compute in FP32.
+enum StoreKind { kStoreF64 = 0, kStoreF32 = 1, kStoreBF16 = 2, kStoreF16 = 3 };
+
+struct StoreF64 {
+  using S = double;
+  using R = double;
+  static constexpr bool dev = false;
+  static constexpr int kind = kStoreF64;
+};
+struct StoreF32 {
+  using S = float;
+  using R = float;
+  static constexpr bool dev = false;
+  static constexpr int kind = kStoreF32;
+};
+struct StoreBF16 {
+  using S = __nv_bfloat16;
+  using R = float;
+  static constexpr bool dev = true;
+  static constexpr int kind = kStoreBF16;
+  static constexpr int qmax_log2 = 0;  // |q| <= 1 (BF16 keeps its exponent range)
+  __device__ static float to_r(S q) { return __bfloat162float(q); }
+  __device__ static S from_r(float v) { return __float2bfloat16_rn(v); }
+};
+struct StoreF16 {
+  using S = __half;
+  using R = float;
+  static constexpr bool dev = true;
+  static constexpr int kind = kStoreF16;
+  static constexpr int qmax_log2 = 15;  // |q| <= 2^15 < 65504
+  __device__ static float to_r(S q) { return __half2float(q); }
+  __device__ static S from_r(float v) { return __float2half_rn(v); }
+};
+
+// Per-velocity constant rows of the velocity table [kVelRows][Qp].
+enum VelRow { kVelEx = 0, kVelEy = 1, kVelW = 2, kVelInvW = 3, kVelWex = 4, kVelWey = 5, kVelRows = 6 };
+
+// Reduction modes for the velocity moments (enum fedbm_reduction).
+enum RedMode { kRedDefault = 0, kRedFP64 = 1, kRedCompFP32 = 2 };
+
+constexpr int kGeoStrideDev = 16;
+
+// Kernel arguments (by value).  Pointers are device pointers of the solver.
+template <typename R>
+struct StageArgs {
+  const void* f_in;         // state read by this stage  [K][Np][Qp] storage type
+  void* f_out;              // state written             [K][Np][Qp]
+  R* res;                   // LSRK residual register     [K][Np][Qp]
+  const float* scale_in;    // deviation forms: per-element scale read  [K]
+  float* scale_out;         // deviation forms: per-element scale written
+  const int32_t* nbr;       // [K][3] face codes
+  const R* geo;             // [K][16] geometry
+  const R* vel;             // [kVelRows][Qp]
+  const R* wall_feq;        // [4][Qp] f^eq(1, u_b) per side
+  const R* wall_den_inv;    // [4] 1 / sum_{e.n<0} |e.n| f^eq(1,u_b) per side
+  int32_t wall_diffuse_mask;  // bit s set: side s is an eq. FullBC wall
+  R W0, W1x, W1y;           // sum w, sum w ex, sum w ey (deviation moments)
+  int64_t K;
+  int32_t Qp;
+  int32_t epc;              // elements per CTA
+  R dt, rkA, rkB, inv_tau, ab;
+  int32_t collision, eq_order, red;
+};
+
+__host__ __device__ constexpr int np_of(int p) { return (p + 1) * (p + 2) / 2; }
+
+// Bytes of dynamic shared memory of one CTA; the layout is mirrored by the
+// kernel's carve-up.
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__host__ inline size_t stage_smem_bytes(int p, int store_kind, int epc, int Qp) {
+  const int Np = np_of(p), Nfp = p + 1;
+  const size_t s_bytes = store_kind == kStoreF64 ? 8 : store_kind == kStoreF32 ? 4 : 2;
+  const size_t r_bytes = store_kind == kStoreF64 ? 8 : 4;
+  const bool dev = store_kind >= kStoreBF16;
+  size_t b = 0;
+  b += align16(size_t(epc) * Np * Qp * s_bytes);     // f tile
+  b += align16(size_t(epc) * kGeoStrideDev * r_bytes);  // geometry
+  b += align16(size_t(epc) * 3 * 4);                 // face codes
+  b += align16(size_t(epc) * 4 * r_bytes);           // element scale (dev)
+  b += align16(size_t(epc) * Np * 4 * r_bytes);      // rho, ux, uy per node
+  b += align16(size_t(epc) * 3 * Nfp * r_bytes);     // wall numerators
+  if (dev) {
+    b += align16(size_t(epc) * Np * Qp * 4);         // new f (FP32) before encoding
+    b += align16(size_t(epc) * 4);                   // max |deviation| per element
+  }
+  return b;
+}
+
+}  // namespace fedbm

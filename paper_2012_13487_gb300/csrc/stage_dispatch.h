@@ -1,0 +1,23 @@
+// Per-degree entry points of the fused stage kernel (one translation unit per
+// polynomial degree, so the degrees compile in parallel).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace fedbm {
+
+struct StageEntry {
+  cudaError_t (*launch)(int store_kind, const void* args, int grid, int block, size_t smem, cudaStream_t st);
+  cudaError_t (*set_smem)(int store_kind, size_t smem);
+  cudaError_t (*upload)(const double* Dr, const double* Ds, const double* LIFT);
+};
+
+StageEntry stage_entry_p0();
+StageEntry stage_entry_p1();
+StageEntry stage_entry_p2();
+StageEntry stage_entry_p3();
+StageEntry stage_entry_p4();
+StageEntry stage_entry_p5();
+StageEntry stage_entry_p6();
+
+}  // namespace fedbm

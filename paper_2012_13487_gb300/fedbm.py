@@ -1,0 +1,291 @@
+"""ctypes binding of ``libfedbm.so`` (C ABI in ``include/fedbm.h``).
+
+Argument marshalling only: every function here forwards to the C entry point
+of the same name; all computation runs in the CUDA library.  PyTorch is used
+only to supply device buffers and streams (``tensor.data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``).  Loading fails loudly if the
+library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfedbm.so")
+
+FEDBM_OK = 0
+FEDBM_EINVAL = -1
+FEDBM_ENOMEM = -2
+FEDBM_ECUDA = -3
+FEDBM_ENONFINITE = -4
+FEDBM_ETIMEOUT = -5
+FEDBM_ENOTSUP = -6
+
+BC_PERIODIC, BC_WALL_DIFFUSE, BC_WALL_EQ = 0, 1, 2
+VELSET_GH, VELSET_NC = 0, 1
+FP64, FP32, BF16_DEV, FP16_DEV = 0, 1, 2, 3
+RED_DEFAULT, RED_FP64, RED_COMP_FP32 = 0, 1, 2
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("bc", ctypes.c_int32 * 4), ("wall_ux", ctypes.c_double * 4),
+                ("wall_uy", ctypes.c_double * 4), ("lx", ctypes.c_double), ("ly", ctypes.c_double)]
+
+
+class VelsetDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("nc_extent", ctypes.c_double),
+                ("nc_sqrt2", ctypes.c_int32), ("eq_order", ctypes.c_int32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("kn", ctypes.c_double), ("length", ctypes.c_double), ("beta", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("reduction", ctypes.c_int32), ("collision", ctypes.c_int32),
+                ("elems_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("Np", ctypes.c_int64), ("Nfp", ctypes.c_int64),
+                ("Q", ctypes.c_int64), ("Q_padded", ctypes.c_int64), ("dt", ctypes.c_double),
+                ("tau", ctypes.c_double), ("time", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("precision", ctypes.c_int32), ("reduction", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("eq_order", ctypes.c_int32), ("elems_per_cta", ctypes.c_int32),
+                ("threads_per_cta", ctypes.c_int32), ("state_bytes", ctypes.c_int64),
+                ("residual_bytes", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+
+# name -> (restype, argtypes); exactly the entry points of include/fedbm.h
+SIGNATURES = {
+    "fedbm_velset": (ctypes.c_int, [ctypes.POINTER(VelsetDesc), _P, _P, _P, _I32]),
+    "fedbm_ref_operators": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P]),
+    "fedbm_mesh_nodes": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.POINTER(VelsetDesc),
+                                        ctypes.POINTER(Params), _P, _P, _D]),
+    "fedbm_mesh_connectivity": (ctypes.c_int, [ctypes.POINTER(MeshDesc), _P]),
+    "fedbm_create": (ctypes.c_int, [ctypes.POINTER(MeshDesc), ctypes.POINTER(VelsetDesc),
+                                    ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
+    "fedbm_destroy": (None, [_P]),
+    "fedbm_set_state": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "fedbm_set_equilibrium": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_uint64]),
+    "fedbm_rk_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "fedbm_rk_stage": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "fedbm_get_moments": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32]),
+    "fedbm_get_state": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "fedbm_get_residual": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "fedbm_mass": (ctypes.c_int, [_P, _D]),
+    "fedbm_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "fedbm_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libfedbm.so once; raise if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libfedbm.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_2012_13487_gb300.build)")
+        L = ctypes.CDLL(_LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class FedbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fedbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(rc):
+    if rc != FEDBM_OK:
+        raise FedbmError(rc, lib().fedbm_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Pointer of a NumPy array or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+# ---- descriptor helpers ------------------------------------------------------
+def mesh_desc(nx, ny, order, bc=(BC_WALL_DIFFUSE, BC_PERIODIC, BC_WALL_DIFFUSE, BC_PERIODIC),
+              wall_u=((0, 0), (0, 0), (0, 0), (0, 0)), lx=1.0, ly=1.0):
+    d = MeshDesc()
+    d.nx, d.ny, d.order = nx, ny, order
+    for s in range(4):
+        d.bc[s] = bc[s]
+        d.wall_ux[s] = wall_u[s][0]
+        d.wall_uy[s] = wall_u[s][1]
+    d.lx, d.ly = lx, ly
+    return d
+
+
+def velset_desc(kind=VELSET_GH, n=4, eq_order=2, nc_extent=4.0, nc_sqrt2=0):
+    d = VelsetDesc()
+    d.kind, d.n, d.eq_order, d.nc_extent, d.nc_sqrt2 = kind, n, eq_order, nc_extent, nc_sqrt2
+    return d
+
+
+def params(kn=1.0, precision=FP32, reduction=RED_DEFAULT, cfl=0.5, dt=0.0, beta=1.0, collision=1,
+           length=1.0, elems_per_cta=0, threads_per_cta=0):
+    p = Params()
+    p.kn, p.length, p.beta, p.cfl, p.dt = kn, length, beta, cfl, dt
+    p.precision, p.reduction, p.collision = precision, reduction, collision
+    p.elems_per_cta, p.threads_per_cta = elems_per_cta, threads_per_cta
+    return p
+
+
+# ---- entry points (same names as the C ABI) ----------------------------------
+def fedbm_velset(vs):
+    q = ctypes.c_int32()
+    _check(lib().fedbm_velset(ctypes.byref(vs), None, None, None, ctypes.byref(q)))
+    ex, ey, w = (np.zeros(q.value) for _ in range(3))
+    _check(lib().fedbm_velset(ctypes.byref(vs), _ptr(ex), _ptr(ey), _ptr(w), ctypes.byref(q)))
+    return ex, ey, w
+
+
+def fedbm_ref_operators(p):
+    Np, Nfp = (p + 1) * (p + 2) // 2, p + 1
+    out = dict(r=np.zeros(Np), s=np.zeros(Np), Dr=np.zeros((Np, Np)), Ds=np.zeros((Np, Np)),
+               LIFT=np.zeros((Np, 3 * Nfp)), M=np.zeros((Np, Np)), fmask=np.zeros((3, Nfp), np.int32))
+    _check(lib().fedbm_ref_operators(p, *(_ptr(out[k]) for k in ("r", "s", "Dr", "Ds", "LIFT", "M", "fmask"))))
+    return out
+
+
+def fedbm_mesh_nodes(mesh, vs=None, prm=None):
+    K = 2 * mesh.nx * mesh.ny
+    Np = (mesh.order + 1) * (mesh.order + 2) // 2
+    x, y = np.zeros((K, Np)), np.zeros((K, Np))
+    dt = ctypes.c_double(0.0)
+    _check(lib().fedbm_mesh_nodes(ctypes.byref(mesh), ctypes.byref(vs) if vs else None,
+                                  ctypes.byref(prm) if prm else None, _ptr(x), _ptr(y),
+                                  ctypes.byref(dt) if (vs and prm) else None))
+    return x, y, dt.value
+
+
+def fedbm_mesh_connectivity(mesh):
+    nbr = np.zeros((2 * mesh.nx * mesh.ny, 3), np.int32)
+    _check(lib().fedbm_mesh_connectivity(ctypes.byref(mesh), _ptr(nbr)))
+    return nbr
+
+
+def fedbm_create(mesh, vs, prm, stream=0):
+    h = ctypes.c_void_p()
+    _check(lib().fedbm_create(ctypes.byref(mesh), ctypes.byref(vs), ctypes.byref(prm),
+                              ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def fedbm_destroy(h):
+    lib().fedbm_destroy(h)
+
+
+def fedbm_set_state(h, f, on_device):
+    _check(lib().fedbm_set_state(h, _ptr(f), int(on_device)))
+
+
+def fedbm_set_equilibrium(h, rho0=1.0, ux0=0.0, uy0=0.0, amp=0.0, seed=0):
+    _check(lib().fedbm_set_equilibrium(h, rho0, ux0, uy0, amp, seed))
+
+
+def fedbm_rk_step(h, nsteps=1):
+    _check(lib().fedbm_rk_step(h, nsteps))
+
+
+def fedbm_rk_stage(h, stage):
+    _check(lib().fedbm_rk_stage(h, stage))
+
+
+def fedbm_get_moments(h, rho, ux, uy, on_device):
+    _check(lib().fedbm_get_moments(h, _ptr(rho), _ptr(ux), _ptr(uy), int(on_device)))
+
+
+def fedbm_get_state(h, f, on_device):
+    _check(lib().fedbm_get_state(h, _ptr(f), int(on_device)))
+
+
+def fedbm_get_residual(h, r, on_device):
+    _check(lib().fedbm_get_residual(h, _ptr(r), int(on_device)))
+
+
+def fedbm_mass(h):
+    m = ctypes.c_double()
+    _check(lib().fedbm_mass(h, ctypes.byref(m)))
+    return m.value
+
+
+def fedbm_info(h):
+    info = Info()
+    _check(lib().fedbm_info(h, ctypes.byref(info)))
+    return info
+
+
+class Solver:
+    """Owning handle: create on construction, destroy on close/garbage collection."""
+
+    def __init__(self, mesh, vs, prm, stream=0):
+        self.h = fedbm_create(mesh, vs, prm, stream)
+        self.info = fedbm_info(self.h)
+
+    @property
+    def shape(self):
+        i = fedbm_info(self.h)
+        return (i.K, i.Np, i.Q)
+
+    def set_state(self, f, on_device=False):
+        fedbm_set_state(self.h, f, on_device)
+
+    def set_equilibrium(self, rho0=1.0, ux0=0.0, uy0=0.0, amp=0.0, seed=0):
+        fedbm_set_equilibrium(self.h, rho0, ux0, uy0, amp, seed)
+
+    def step(self, n=1):
+        fedbm_rk_step(self.h, n)
+
+    def stage(self, s):
+        fedbm_rk_stage(self.h, s)
+
+    def state(self):
+        f = np.zeros(self.shape)
+        fedbm_get_state(self.h, f, False)
+        return f
+
+    def residual(self):
+        r = np.zeros(self.shape)
+        fedbm_get_residual(self.h, r, False)
+        return r
+
+    def moments(self):
+        K, Np, _ = self.shape
+        rho, ux, uy = np.zeros((K, Np)), np.zeros((K, Np)), np.zeros((K, Np))
+        fedbm_get_moments(self.h, rho, ux, uy, False)
+        return rho, ux, uy
+
+    def mass(self):
+        return fedbm_mass(self.h)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            fedbm_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

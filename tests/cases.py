@@ -1,0 +1,49 @@
+"""Test cases: one description builds both the oracle problem and the CUDA solver."""
+import numpy as np
+
+from oracle import dg
+from paper_2012_13487_gb300 import inputs
+
+BC_CODE = {"periodic": 0, "diffuse": 1, "eq": 2}
+PREC_CODE = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
+RED_CODE = {"default": 0, "fp64": 1, "comp": 2}
+
+COUETTE_BC = ("diffuse", "periodic", "diffuse", "periodic")
+CAVITY_BC = ("diffuse",) * 4
+
+
+def couette(nx, ny, p, U=0.1, **kw):
+    return dict(nx=nx, ny=ny, p=p, bc=COUETTE_BC, wall_u=((-U, 0), (0, 0), (U, 0), (0, 0)), **kw)
+
+
+def cavity(nx, ny, p, U=0.1, **kw):
+    return dict(nx=nx, ny=ny, p=p, bc=CAVITY_BC, wall_u=((0, 0), (0, 0), (U, 0), (0, 0)), **kw)
+
+
+def oracle_problem(c):
+    vs = c.get("velset", ("gh", 4))
+    return dg.Problem(c["nx"], c["ny"], c["p"], velset=vs, eq_order=c.get("eq_order", 2),
+                      kn=c.get("kn", 1.0), beta=c.get("beta", 1.0), bc=c["bc"], wall_u=c["wall_u"],
+                      cfl=c.get("cfl", 0.5), collision=c.get("collision", True),
+                      nc_scale=np.sqrt(2.0) if c.get("nc_sqrt2", False) else 1.0)
+
+
+def solver(c, precision="fp32", reduction="default", **tile):
+    from paper_2012_13487_gb300 import fedbm as fb
+    vs = c.get("velset", ("gh", 4))
+    m = fb.mesh_desc(c["nx"], c["ny"], c["p"], bc=tuple(BC_CODE[b] for b in c["bc"]), wall_u=c["wall_u"])
+    v = fb.velset_desc(fb.VELSET_GH if vs[0] == "gh" else fb.VELSET_NC, vs[1], c.get("eq_order", 2),
+                       nc_sqrt2=int(c.get("nc_sqrt2", False)))
+    prm = fb.params(kn=c.get("kn", 1.0), precision=PREC_CODE[precision], reduction=RED_CODE[reduction],
+                    cfl=c.get("cfl", 0.5), beta=c.get("beta", 1.0), collision=int(c.get("collision", True)),
+                    elems_per_cta=tile.get("epc", 0), threads_per_cta=tile.get("tpb", 0))
+    return fb.Solver(m, v, prm)
+
+
+def initial_state(pr, amp=1e-3, seed=201213487, rho0=1.0, ux0=0.0, uy0=0.0):
+    u = inputs.perturbation(seed, pr.K, pr.Np, pr.Q)
+    return pr.equilibrium_state(rho0, ux0, uy0, amp, u)
+
+
+def rel_max_err(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
