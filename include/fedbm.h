@@ -105,7 +105,8 @@ typedef struct fedbm_params {
   int32_t reduction;     /* enum fedbm_reduction                                */
   int32_t collision;     /* 1: BGK collision on; 0: pure advection              */
   int32_t elems_per_cta; /* stage-kernel tile: elements per CTA (0 = auto)      */
-  int32_t threads_per_cta; /* stage-kernel tile: threads per CTA (0 = auto)     */
+  int32_t threads_per_cta; /* stage-kernel tile: threads per CTA, multiple of 32,
+                            <= 256 (0 = auto)                                  */
 } fedbm_params;
 
 typedef struct fedbm_info_t {

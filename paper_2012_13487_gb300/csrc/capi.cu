@@ -295,7 +295,7 @@ struct fedbm_solver {
   double* staging = nullptr;         // canonical FP64 [K][Np][Q] (lazy)
   double* mom = nullptr;             // [3][K][Np] (lazy)
   double* partial = nullptr;         // [kMassBlocks + 1]
-  int* flag = nullptr;
+  int* flag = nullptr;               // [0]: mass diagnostic flag, [1]: stage-kernel wait timeout
   int wall_diffuse_mask = 0;
   double W0 = 0, W1x = 0, W1y = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -330,6 +330,7 @@ void fill_stage_args(const fedbm_solver* s, int stage, int from, StageArgs<R>& a
   a.collision = s->prm.collision;
   a.eq_order = s->vs_desc.eq_order;
   a.red = s->prm.reduction;
+  a.err = s->flag + 1;
 }
 
 cudaError_t launch_stage(const fedbm_solver* s, int stage, int from, cudaStream_t st) {
@@ -529,7 +530,7 @@ extern "C" int fedbm_create(const fedbm_mesh_desc* md, const fedbm_velset_desc* 
   } else {
     s->tpb = std::min(256, std::max(32, (s->epc * s->Qp + 31) / 32 * 32));
   }
-  if (s->tpb % 32 || s->tpb > 512) return bail(fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 512"));
+  if (s->tpb % 32 || s->tpb > 256) return bail(fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256"));
   s->smem = stage_smem_bytes(md->order, s->store, s->epc, s->Qp);
   if (s->smem > 227 * 1024) return bail(fail(FEDBM_EINVAL, "stage tile does not fit in shared memory"));
 
@@ -602,8 +603,8 @@ extern "C" int fedbm_create(const fedbm_mesh_desc* md, const fedbm_velset_desc* 
            if ((rc = upload_real<float>(wden, &s->wall_den_inv)) != FEDBM_OK) return rc;
          }
          FEDBM_CK(cudaMalloc(&s->partial, (kMassBlocks + 1) * sizeof(double)));
-         FEDBM_CK(cudaMalloc(&s->flag, sizeof(int)));
-         FEDBM_CK(cudaMemset(s->flag, 0, sizeof(int)));
+         FEDBM_CK(cudaMalloc(&s->flag, 2 * sizeof(int)));
+         FEDBM_CK(cudaMemset(s->flag, 0, 2 * sizeof(int)));
          return FEDBM_OK;
        }()) != FEDBM_OK)
     return bail(rc);
@@ -757,11 +758,12 @@ extern "C" int fedbm_mass(fedbm_solver* s, double* total) {
   FEDBM_CK(cudaGetLastError());
   mass_final_kernel<<<1, 256, 0, s->stream>>>(s->partial, g, s->partial + kMassBlocks);
   FEDBM_CK(cudaGetLastError());
-  int flag = 0;
+  int flag[2] = {0, 0};
   FEDBM_CK(cudaMemcpyAsync(total, s->partial + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  FEDBM_CK(cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  FEDBM_CK(cudaMemcpyAsync(flag, s->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   FEDBM_CK(cudaStreamSynchronize(s->stream));
-  if (flag) return fail(FEDBM_ENONFINITE, "state has a non-finite value or a node with rho <= 0");
+  if (flag[1]) return fail(FEDBM_ETIMEOUT, "a stage kernel's bounded wait for its tile copies gave up");
+  if (flag[0]) return fail(FEDBM_ENONFINITE, "state has a non-finite value or a node with rho <= 0");
   return FEDBM_OK;
 }
 

@@ -71,31 +71,74 @@ struct StageArgs {
   int32_t epc;              // elements per CTA
   R dt, rkA, rkB, inv_tau, ab;
   int32_t collision, eq_order, red;
+  int* err;                 // set to 1 if a bounded wait of a CTA gave up
 };
 
 __host__ __device__ constexpr int np_of(int p) { return (p + 1) * (p + 2) / 2; }
 
-// Bytes of dynamic shared memory of one CTA; the layout is mirrored by the
-// kernel's carve-up.
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
+// Shared-memory layout of one stage CTA (offsets in bytes); the host sizes the
+// launch with it and the kernel carves its buffers with it.
+enum SmemPart { kSmBar, kSmF, kSmRes, kSmTr, kSmGeo, kSmNbr, kSmScale, kSmNScale, kSmDmax, kSmMom, kSmWn, kSmEnd };
+
+__host__ __device__ inline size_t stage_smem_layout(int Np, int NF, int epc, int Qp, size_t s_bytes, size_t r_bytes,
+                                                    size_t off[kSmEnd + 1]) {
+  size_t b = 0;
+  off[kSmBar] = b;    b += 16;
+  off[kSmF] = b;      b += align16(size_t(epc) * Np * Qp * s_bytes);   // element tile (updated in place)
+  off[kSmRes] = b;    b += align16(size_t(epc) * Np * Qp * r_bytes);   // residual tile (updated in place)
+  off[kSmTr] = b;     b += align16(size_t(epc) * NF * Qp * s_bytes);   // neighbour face traces
+  off[kSmGeo] = b;    b += align16(size_t(epc) * kGeoStrideDev * r_bytes);
+  off[kSmNbr] = b;    b += align16(size_t(epc) * 3 * 4);
+  off[kSmScale] = b;  b += align16(size_t(epc) * 4);                  // element scale (deviation forms)
+  off[kSmNScale] = b; b += align16(size_t(epc) * 3 * 4);              // neighbour scales, then new scale
+  off[kSmDmax] = b;   b += align16(size_t(epc) * 4);
+  off[kSmMom] = b;    b += align16(size_t(epc) * Np * 4 * r_bytes);   // rho, ux, uy per node
+  off[kSmWn] = b;     b += align16(size_t(epc) * NF * r_bytes);        // wall numerators
+  off[kSmEnd] = b;
+  return b;
+}
+
+template <typename R, typename S>
+struct StageSmem {
+  uint64_t* bar;
+  S* f;
+  R* res;
+  S* tr;
+  R* geo;
+  int* nbr;
+  float* scale;
+  float* nscale;
+  unsigned* dmax;
+  R* mom;
+  R* wn;
+};
+
+template <typename R, typename S>
+__device__ inline StageSmem<R, S> carve_stage_smem(unsigned char* base, int Np, int NF, int epc, int Qp) {
+  size_t off[kSmEnd + 1];
+  stage_smem_layout(Np, NF, epc, Qp, sizeof(S), sizeof(R), off);
+  StageSmem<R, S> s;
+  s.bar = reinterpret_cast<uint64_t*>(base + off[kSmBar]);
+  s.f = reinterpret_cast<S*>(base + off[kSmF]);
+  s.res = reinterpret_cast<R*>(base + off[kSmRes]);
+  s.tr = reinterpret_cast<S*>(base + off[kSmTr]);
+  s.geo = reinterpret_cast<R*>(base + off[kSmGeo]);
+  s.nbr = reinterpret_cast<int*>(base + off[kSmNbr]);
+  s.scale = reinterpret_cast<float*>(base + off[kSmScale]);
+  s.nscale = reinterpret_cast<float*>(base + off[kSmNScale]);
+  s.dmax = reinterpret_cast<unsigned*>(base + off[kSmDmax]);
+  s.mom = reinterpret_cast<R*>(base + off[kSmMom]);
+  s.wn = reinterpret_cast<R*>(base + off[kSmWn]);
+  return s;
+}
+
 __host__ inline size_t stage_smem_bytes(int p, int store_kind, int epc, int Qp) {
-  const int Np = np_of(p), Nfp = p + 1;
   const size_t s_bytes = store_kind == kStoreF64 ? 8 : store_kind == kStoreF32 ? 4 : 2;
   const size_t r_bytes = store_kind == kStoreF64 ? 8 : 4;
-  const bool dev = store_kind >= kStoreBF16;
-  size_t b = 0;
-  b += align16(size_t(epc) * Np * Qp * s_bytes);     // f tile
-  b += align16(size_t(epc) * kGeoStrideDev * r_bytes);  // geometry
-  b += align16(size_t(epc) * 3 * 4);                 // face codes
-  b += align16(size_t(epc) * 4 * r_bytes);           // element scale (dev)
-  b += align16(size_t(epc) * Np * 4 * r_bytes);      // rho, ux, uy per node
-  b += align16(size_t(epc) * 3 * Nfp * r_bytes);     // wall numerators
-  if (dev) {
-    b += align16(size_t(epc) * Np * Qp * 4);         // new f (FP32) before encoding
-    b += align16(size_t(epc) * 4);                   // max |deviation| per element
-  }
-  return b;
+  size_t off[kSmEnd + 1];
+  return stage_smem_layout(np_of(p), 3 * (p + 1), epc, Qp, s_bytes, r_bytes, off);
 }
 
 }  // namespace fedbm

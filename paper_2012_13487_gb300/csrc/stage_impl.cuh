@@ -111,37 +111,108 @@ __device__ __forceinline__ typename ST::R decode(const typename ST::S v, typenam
   }
 }
 
-// Phase 2: rho, u_x, u_y of every node of the tile into s_mom.
+// ---- asynchronous bulk copies (TMA, non-tensor) and their mbarrier -----------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the barrier for at most `limit_ns`; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_timer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst_smem)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src_smem)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit_and_wait_read() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Vector of the storage type covering 16 bytes.
+template <class ST>
+struct Vec16 {
+  static constexpr int N = 16 / int(sizeof(typename ST::S));
+};
+
+// Phase 2: rho, u_x, u_y of every node of the tile into s_mom.  G lanes share a
+// node; each lane reduces 16-byte chunks of the node's velocity row.
 template <class ST, class Acc>
 __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename ST::S* s_f,
-                             const typename ST::R* s_scale, typename ST::R* s_mom, int ne) {
+                             const float* s_scale, typename ST::R* s_mom, int ne) {
   using R = typename ST::R;
+  using S = typename ST::S;
+  constexpr int V = Vec16<ST>::N;
   const int Qp = a.Qp, tid = threadIdx.x, nth = blockDim.x;
-  const int G = pow2_floor_32(nth / (a.epc * NP));
+  const int nchunk = Qp / V;
+  int G = pow2_floor_32(nth / (a.epc * NP));
+  while (G > 1 && G > nchunk) G >>= 1;
   const int ngroups = nth / G, grp = tid / G, lane = tid % G;
   const int npair = ne * NP;
   const R* ex = a.vel + kVelEx * Qp;
   const R* ey = a.vel + kVelEy * Qp;
   const R* wv = a.vel + kVelW * Qp;
-  const R* wex = a.vel + kVelWex * Qp;
-  const R* wey = a.vel + kVelWey * Qp;
   for (int base = 0; base < npair; base += ngroups) {
     const int pair = base + grp;
     const bool valid = pair < npair;
     Acc m0, m1, m2;
     if (valid) {
-      const typename ST::S* row = s_f + size_t(pair) * Qp;
-      for (int i = lane; i < Qp; i += G) {
-        if constexpr (ST::dev) {
-          const float q = ST::to_r(row[i]);
-          m0.add(wv[i] * q);
-          m1.add(wex[i] * q);
-          m2.add(wey[i] * q);
-        } else {
-          const R f = row[i];
-          m0.add(f);
-          m1.add(ex[i] * f);
-          m2.add(ey[i] * f);
+      const S* row = s_f + size_t(pair) * Qp;
+      for (int c = lane; c < nchunk; c += G) {
+        __align__(16) S v[V];
+        *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(row + c * V);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const int i = c * V + j;
+          if constexpr (ST::dev) {
+            const float wq = __ldg(wv + i) * ST::to_r(v[j]);
+            m0.add(wq);
+            m1.add(__ldg(ex + i) * wq);
+            m2.add(__ldg(ey + i) * wq);
+          } else {
+            const R f = v[j];
+            m0.add(f);
+            m1.add(__ldg(ex + i) * f);
+            m2.add(__ldg(ey + i) * f);
+          }
         }
       }
     }
@@ -172,7 +243,7 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
 template <class ST>
 __device__ void tile_wall_numerators(const StageArgs<typename ST::R>& a, const typename ST::S* s_f,
                                      const typename ST::R* s_geo, const int* s_nbr,
-                                     const typename ST::R* s_scale, typename ST::R* s_wn, int ne) {
+                                     const float* s_scale, typename ST::R* s_wn, int ne) {
   using R = typename ST::R;
   const int Qp = a.Qp, tid = threadIdx.x, nth = blockDim.x;
   const int G = pow2_floor_32(nth / (a.epc * NF));
@@ -189,17 +260,18 @@ __device__ void tile_wall_numerators(const StageArgs<typename ST::R>& a, const t
       const int code = s_nbr[e * 3 + fc];
       active = code < 0 && ((a.wall_diffuse_mask >> (-code - 1)) & 1);
     }
-    typename ST::R acc = 0;
+    R acc = 0;
     if (active) {
       const R nxf = s_geo[e * kGeoStrideDev + 4 + 3 * fc];
       const R nyf = s_geo[e * kGeoStrideDev + 5 + 3 * fc];
-      const int node = (fc == 0) ? aa : (fc == 1 ? aa * (P + 1) - aa * (aa - 1) / 2 + (P - aa)
-                                                 : aa * (P + 1) - aa * (aa - 1) / 2);
+      const int rs = aa * (P + 1) - aa * (aa - 1) / 2;
+      const int node = (fc == 0) ? aa : (fc == 1 ? rs + (P - aa) : rs);
       const typename ST::S* row = s_f + (size_t(e) * NP + node) * Qp;
       const R sc = ST::dev ? s_scale[e] : R(0);
       for (int i = lane; i < Qp; i += G) {
-        const R en = ex[i] * nxf + ey[i] * nyf;
-        if (en > 0) acc += en * decode<ST>(row[i], wv[i], wv[i] * sc);
+        const R en = __ldg(ex + i) * nxf + __ldg(ey + i) * nyf;
+        const R w = __ldg(wv + i);
+        if (en > 0) acc += en * decode<ST>(row[i], w, w * sc);
       }
     }
     for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
@@ -207,119 +279,145 @@ __device__ void tile_wall_numerators(const StageArgs<typename ST::R>& a, const t
   }
 }
 
+// new f of one value: decode, then f + B res (shared by the update and the
+// encoding pass of the deviation forms so both see the same rounding)
 template <class ST>
-__global__ void __launch_bounds__(512) stage_kernel(const StageArgs<typename ST::R> a) {
+__device__ __forceinline__ typename ST::R new_f(typename ST::R fold, typename ST::R rkB, typename ST::R r) {
+  return fma(rkB, r, fold);
+}
+
+// Minimum resident CTAs of 256 threads per SM: bounds the registers per thread
+// (65536 / (256 * min)) so that the unrolled node loop does not spill.
+template <class ST>
+constexpr int stage_min_blocks() {
+  return sizeof(typename ST::R) == 8 ? 2 : (P <= 3 ? 4 : (P <= 5 ? 3 : 2));
+}
+
+template <class ST>
+__global__ void __launch_bounds__(256, stage_min_blocks<ST>()) stage_kernel(const StageArgs<typename ST::R> a) {
   using R = typename ST::R;
   using S = typename ST::S;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int epc = a.epc, Qp = a.Qp;
   const int64_t k0 = int64_t(blockIdx.x) * epc;
   const int ne = int(min(int64_t(epc), a.K - k0));
   const int tid = threadIdx.x, nth = blockDim.x;
+  const R rkA = a.rkA;
+  const bool read_res = rkA != R(0);
 
-  unsigned char* p = smem;
-  S* s_f = reinterpret_cast<S*>(p);
-  p += align16(size_t(epc) * NP * Qp * sizeof(S));
-  R* s_geo = reinterpret_cast<R*>(p);
-  p += align16(size_t(epc) * kGeoStrideDev * sizeof(R));
-  int* s_nbr = reinterpret_cast<int*>(p);
-  p += align16(size_t(epc) * 3 * 4);
-  R* s_scale = reinterpret_cast<R*>(p);
-  p += align16(size_t(epc) * 4 * sizeof(R));
-  R* s_mom = reinterpret_cast<R*>(p);
-  p += align16(size_t(epc) * NP * 4 * sizeof(R));
-  R* s_wn = reinterpret_cast<R*>(p);
-  p += align16(size_t(epc) * NF * sizeof(R));
-  float* s_fnew = nullptr;
-  unsigned* s_max = nullptr;
-  if constexpr (ST::dev) {
-    s_fnew = reinterpret_cast<float*>(p);
-    p += align16(size_t(epc) * NP * Qp * 4);
-    s_max = reinterpret_cast<unsigned*>(p);
+  StageSmem<R, S> sm = carve_stage_smem<R, S>(smem, NP, NF, epc, Qp);
+  const S* fin = static_cast<const S*>(a.f_in);
+  const size_t row_bytes = size_t(Qp) * sizeof(S);
+
+  if (tid == 0) {
+    mbar_init(sm.bar, 32);
+    fence_mbar_init();
+    fence_proxy_async_smem();
   }
+  __syncthreads();
 
-  // ---- 1. tile load --------------------------------------------------------
-  {
-    const S* fin = static_cast<const S*>(a.f_in);
-    const size_t nvec = size_t(ne) * NP * Qp * sizeof(S) / 16;
-    const uint4* src = reinterpret_cast<const uint4*>(fin + k0 * NP * Qp);
-    uint4* dst = reinterpret_cast<uint4*>(s_f);
-    for (size_t v = tid; v < nvec; v += nth) dst[v] = __ldg(src + v);
-    for (int v = tid; v < ne * kGeoStrideDev; v += nth) s_geo[v] = a.geo[k0 * kGeoStrideDev + v];
-    for (int v = tid; v < ne * 3; v += nth) s_nbr[v] = a.nbr[k0 * 3 + v];
-    if constexpr (ST::dev) {
-      for (int v = tid; v < ne; v += nth) {
-        s_scale[v] = a.scale_in[k0 + v];
-        s_max[v] = 0u;
+  // ---- 1. asynchronous tile load: element tile, residual tile, face traces ----
+  if (tid < 32) {
+    uint32_t bytes = 0;
+    const uint32_t tile_bytes = uint32_t(size_t(ne) * NP * row_bytes);
+    if (tid == 0) bytes += tile_bytes + (read_res ? uint32_t(size_t(ne) * NP * Qp * sizeof(R)) : 0u);
+    for (int row = tid; row < ne * NF; row += 32) {
+      const int code = __ldg(a.nbr + (k0 + row / NF) * 3 + (row % NF) / NFP);
+      if (code >= 0) bytes += uint32_t(row_bytes);
+    }
+    mbar_arrive_expect_tx(sm.bar, bytes);
+    if (tid == 0) {
+      bulk_load(sm.f, fin + k0 * NP * Qp, tile_bytes, sm.bar);
+      if (read_res) bulk_load(sm.res, a.res + k0 * NP * Qp, uint32_t(size_t(ne) * NP * Qp * sizeof(R)), sm.bar);
+    }
+    for (int row = tid; row < ne * NF; row += 32) {
+      const int e = row / NF, fc = (row % NF) / NFP, aa = row % NFP;
+      const int code = __ldg(a.nbr + (k0 + e) * 3 + fc);
+      if (code >= 0) {
+        const int64_t kn = code >> 3;
+        const int fn = (code >> 1) & 3;
+        const int a2 = (code & 1) ? NFP - 1 - aa : aa;
+        const int rs = a2 * (P + 1) - a2 * (a2 - 1) / 2;
+        const int node = fn == 0 ? a2 : (fn == 1 ? rs + (P - a2) : rs);
+        bulk_load(sm.tr + size_t(row) * Qp, fin + (kn * NP + node) * Qp, uint32_t(row_bytes), sm.bar);
       }
     }
   }
+  for (int v = tid; v < ne * kGeoStrideDev; v += nth) sm.geo[v] = a.geo[k0 * kGeoStrideDev + v];
+  for (int v = tid; v < ne * 3; v += nth) {
+    const int code = a.nbr[k0 * 3 + v];
+    sm.nbr[v] = code;
+    if constexpr (ST::dev) sm.nscale[v] = code >= 0 ? a.scale_in[code >> 3] : 0.f;
+  }
+  if constexpr (ST::dev) {
+    for (int v = tid; v < ne; v += nth) {
+      sm.scale[v] = a.scale_in[k0 + v];
+      sm.dmax[v] = 0u;
+    }
+  }
   __syncthreads();
+  if (!mbar_wait_bounded(sm.bar, 0, 2000000000ull)) {
+    if (a.err) atomicExch(a.err, 1);
+    mbar_wait_bounded(sm.bar, 0, 1000000000ull);  // let copies in flight land before exit
+    return;
+  }
 
   // ---- 2. node moments ---------------------------------------------------------
   if (a.collision) {
     if constexpr (sizeof(R) == 8) {
-      tile_moments<ST, AccD>(a, s_f, s_scale, s_mom, ne);
+      tile_moments<ST, AccD>(a, sm.f, sm.scale, sm.mom, ne);
     } else {
-      if (a.red == kRedFP64) tile_moments<ST, AccD>(a, s_f, s_scale, s_mom, ne);
-      else if (a.red == kRedCompFP32) tile_moments<ST, AccN>(a, s_f, s_scale, s_mom, ne);
-      else tile_moments<ST, AccF>(a, s_f, s_scale, s_mom, ne);
+      if (a.red == kRedFP64) tile_moments<ST, AccD>(a, sm.f, sm.scale, sm.mom, ne);
+      else if (a.red == kRedCompFP32) tile_moments<ST, AccN>(a, sm.f, sm.scale, sm.mom, ne);
+      else tile_moments<ST, AccF>(a, sm.f, sm.scale, sm.mom, ne);
     }
   }
   // ---- 3. wall numerators ------------------------------------------------------
-  if (a.wall_diffuse_mask) tile_wall_numerators<ST>(a, s_f, s_geo, s_nbr, s_scale, s_wn, ne);
+  if (a.wall_diffuse_mask) tile_wall_numerators<ST>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, ne);
   __syncthreads();
 
   // ---- 4. residual and update per (element, velocity) ---------------------------
-  const R dt = a.dt, rkA = a.rkA, rkB = a.rkB, ab = a.ab, inv_tau = a.inv_tau;
-  const S* fin = static_cast<const S*>(a.f_in);
+  const R dt = a.dt, rkB = a.rkB, ab = a.ab, inv_tau = a.inv_tau;
   float dmax = 0.f;
   int emax = -1;
-  for (int item = tid; item < epc * Qp; item += nth) {
+  for (int item = tid; item < ne * Qp; item += nth) {
     const int e = item / Qp;
     const int i = item - e * Qp;
-    if (e >= ne) break;
-    const int64_t k = k0 + e;
-    const R ex = a.vel[kVelEx * Qp + i], ey = a.vel[kVelEy * Qp + i], w = a.vel[kVelW * Qp + i];
-    const R* g = s_geo + e * kGeoStrideDev;
+    const R ex = __ldg(a.vel + kVelEx * Qp + i), ey = __ldg(a.vel + kVelEy * Qp + i);
+    const R w = __ldg(a.vel + kVelW * Qp + i);
+    const R* g = sm.geo + e * kGeoStrideDev;
     const R ar = ex * g[0] + ey * g[2];
     const R as = ex * g[1] + ey * g[3];
     R ws = 0;
-    if constexpr (ST::dev) ws = w * s_scale[e];
+    if constexpr (ST::dev) ws = w * sm.scale[e];
+    S* frow = sm.f + size_t(e) * NP * Qp + i;
+    R* rrow = sm.res + size_t(e) * NP * Qp + i;
 
     R fr[NP];
 #pragma unroll
-    for (int m = 0; m < NP; ++m) fr[m] = decode<ST>(s_f[(size_t(e) * NP + m) * Qp + i], w, ws);
+    for (int m = 0; m < NP; ++m) fr[m] = decode<ST>(frow[m * Qp], w, ws);
 
     R flux[NF];
 #pragma unroll
     for (int fc = 0; fc < 3; ++fc) {
       const R en = ex * g[4 + 3 * fc] + ey * g[5 + 3 * fc];
       const R c = R(0.5) * (en - ab * fabs(en)) * g[6 + 3 * fc];
-      const int code = s_nbr[e * 3 + fc];
-      if (c != R(0) && code >= 0) {
-        const int64_t kn = code >> 3;
-        const int fn = (code >> 1) & 3;
-        const int rv = code & 1;
-        const S* nb = fin + kn * NP * Qp + i;
+      const int code = sm.nbr[e * 3 + fc];
+      if (code >= 0) {
         R wsn = 0;
-        if constexpr (ST::dev) wsn = w * __ldg(a.scale_in + kn);
+        if constexpr (ST::dev) wsn = w * sm.nscale[e * 3 + fc];
+        const S* trow = sm.tr + size_t(e * NF + fc * NFP) * Qp + i;
 #pragma unroll
-        for (int aa = 0; aa < NFP; ++aa) {
-          const int a2 = rv ? NFP - 1 - aa : aa;
-          const int rs = a2 * (P + 1) - a2 * (a2 - 1) / 2;
-          const int node = fn == 0 ? a2 : (fn == 1 ? rs + (P - a2) : rs);
-          const R fp = decode<ST>(__ldg(nb + size_t(node) * Qp), w, wsn);
-          flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - fp);
-        }
-      } else if (c != R(0) && en < R(0)) {
+        for (int aa = 0; aa < NFP; ++aa)
+          flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - decode<ST>(trow[aa * Qp], w, wsn));
+      } else if (en < R(0)) {
         const int side = -code - 1;
-        const R fb = a.wall_feq[side * Qp + i];
+        const R fb = __ldg(a.wall_feq + side * Qp + i);
         const bool diffuse = (a.wall_diffuse_mask >> side) & 1;
-        const R scale = diffuse ? a.wall_den_inv[side] * fb : R(0);
+        const R scale = diffuse ? __ldg(a.wall_den_inv + side) * fb : R(0);
 #pragma unroll
         for (int aa = 0; aa < NFP; ++aa) {
-          const R fp = diffuse ? s_wn[e * NF + fc * NFP + aa] * scale : fb;
+          const R fp = diffuse ? sm.wn[e * NF + fc * NFP + aa] * scale : fb;
           flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - fp);
         }
       } else {
@@ -328,9 +426,9 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs<typename ST:
       }
     }
 
-    const int64_t gbase = k * NP * Qp + i;
     float dloc = 0.f;
-    const R invw = ST::dev ? a.vel[kVelInvW * Qp + i] : R(0);
+    R invw = 0;
+    if constexpr (ST::dev) invw = __ldg(a.vel + kVelInvW * Qp + i);
 #pragma unroll
     for (int n = 0; n < NP; ++n) {
       R dr = 0, ds = 0;
@@ -344,28 +442,26 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs<typename ST:
       for (int j = 0; j < NF; ++j) lf = fma(opv<R>(OFF_LIFT + n * NF + j), flux[j], lf);
       R rhs = lf - (ar * dr + as * ds);
       if (a.collision) {
-        const R* mm = s_mom + (size_t(e) * NP + n) * 4;
+        const R* mm = sm.mom + (size_t(e) * NP + n) * 4;
         const R rho = mm[0], ux = mm[1], uy = mm[2];
         const R eu = ex * ux + ey * uy, uu = ux * ux + uy * uy;
         R poly = R(1) + eu + R(0.5) * (eu * eu - uu);
         if (a.eq_order == 3) poly += eu * (eu * eu * R(1.0 / 6.0) - R(0.5) * uu);
         rhs -= (fr[n] - w * rho * poly) * inv_tau;
       }
-      const int64_t gi = gbase + int64_t(n) * Qp;
       R r = dt * rhs;
-      if (rkA != R(0)) r = fma(rkA, a.res[gi], r);
-      a.res[gi] = r;
-      const R fnew = fma(rkB, r, fr[n]);
+      if (read_res) r = fma(rkA, rrow[n * Qp], r);
+      rrow[n * Qp] = r;
+      const R fnew = new_f<ST>(fr[n], rkB, r);
       if constexpr (ST::dev) {
-        s_fnew[(size_t(e) * NP + n) * Qp + i] = fnew;
         dloc = fmaxf(dloc, fabsf((fnew - w) * invw));
       } else {
-        static_cast<S*>(a.f_out)[gi] = S(fnew);
+        frow[n * Qp] = S(fnew);
       }
     }
     if constexpr (ST::dev) {
       if (e != emax) {
-        if (emax >= 0) atomicMax(&s_max[emax], __float_as_uint(dmax));
+        if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
         emax = e;
         dmax = 0.f;
       }
@@ -373,38 +469,51 @@ __global__ void __launch_bounds__(512) stage_kernel(const StageArgs<typename ST:
     }
   }
 
-  // ---- 5. deviation forms: new per-element scale and encoding ------------------
+  // ---- 5. deviation forms: new per-element scale, encoding in place ------------
   if constexpr (ST::dev) {
-    if (emax >= 0) atomicMax(&s_max[emax], __float_as_uint(dmax));
+    if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
     __syncthreads();
     for (int e = tid; e < ne; e += nth) {
-      const float md = __uint_as_float(s_max[e]);
+      const float md = __uint_as_float(sm.dmax[e]);
       float sc = 1.0f;
       if (md > 0.f) {
         int ex2;
         frexpf(md, &ex2);
         sc = ldexpf(1.0f, ex2 - ST::qmax_log2);
       }
-      s_scale[e] = sc;
+      sm.nscale[e] = sc;  // face scales are no longer needed
       a.scale_out[k0 + e] = sc;
     }
     __syncthreads();
-    const int nvec = ne * NP * Qp / 8;
-    S* fout = static_cast<S*>(a.f_out) + k0 * NP * Qp;
+    constexpr int V = Vec16<ST>::N;
+    const int nvec = ne * NP * Qp / V;
     for (int v = tid; v < nvec; v += nth) {
-      const int idx = v * 8;
+      const int idx = v * V;
       const int e = idx / (NP * Qp);
       const int i0 = idx % Qp;
-      const float inv_s = 1.0f / s_scale[e];
-      __align__(16) S q[8];
+      const float sold = sm.scale[e];
+      const float inv_s = 1.0f / sm.nscale[e];
+      __align__(16) S q[V];
+      *reinterpret_cast<uint4*>(q) = *reinterpret_cast<const uint4*>(sm.f + idx);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float w = a.vel[kVelW * Qp + i0 + j];
-        const float invw = a.vel[kVelInvW * Qp + i0 + j];
-        q[j] = ST::from_r((s_fnew[idx + j] - w) * invw * inv_s);
+      for (int j = 0; j < V; ++j) {
+        const float w = __ldg(a.vel + kVelW * Qp + i0 + j);
+        const float invw = __ldg(a.vel + kVelInvW * Qp + i0 + j);
+        const float fold = decode<ST>(q[j], w, w * sold);
+        const float fnew = new_f<ST>(fold, rkB, sm.res[idx + j]);
+        q[j] = ST::from_r((fnew - w) * invw * inv_s);
       }
-      reinterpret_cast<uint4*>(fout)[v] = *reinterpret_cast<const uint4*>(q);
+      *reinterpret_cast<uint4*>(sm.f + idx) = *reinterpret_cast<const uint4*>(q);
     }
+  }
+
+  // ---- 6. bulk store of the new state and residual tiles -------------------------
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    bulk_store(static_cast<S*>(a.f_out) + k0 * NP * Qp, sm.f, uint32_t(size_t(ne) * NP * row_bytes));
+    bulk_store(a.res + k0 * NP * Qp, sm.res, uint32_t(size_t(ne) * NP * Qp * sizeof(R)));
+    bulk_commit_and_wait_read();
   }
 }
 
