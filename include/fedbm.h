@@ -199,6 +199,31 @@ int fedbm_mass(fedbm_solver* s, double* total_mass);
 
 int fedbm_info(const fedbm_solver* s, fedbm_info_t* info);
 
+/* Allocation-free mass diagnostic.  The paper has no counterpart; this entry
+ * point serves callers that must not allocate device memory once they are
+ * running -- an application whose device memory belongs to another allocator
+ * (a framework's caching allocator or a fixed pre-reserved pool), or a
+ * real-time loop that cannot pay for cudaMalloc's latency and implicit device
+ * synchronisation.  It computes the same FP64 sum as fedbm_mass,
+ *     total = sum_k jac[k] * sum_n mass_colsum[n] * sum_i f[k][n][i],
+ * from caller-owned device buffers: f canonical FP64 [K][Np][Q], jac [K]
+ * (element Jacobians, area / 2), mass_colsum [Np] (column sums 1^T M of the
+ * reference mass matrix, see fedbm_ref_operators), and writes total[0] and
+ * status[0] (0 = fine, 1 = a node has a non-finite value or rho <= 0) to
+ * device memory, asynchronously on cuda_stream (NULL = default stream).
+ * It calls no cudaMalloc/cudaFree: its scratch (one FP64 partial sum per 256
+ * nodes plus a status word, 65,792 bytes) is a fixed __device__ array that
+ * every GPU loading the library holds until the process exits.  Capacity:
+ * K * Np <= 2,097,152 nodes; larger inputs return FEDBM_EINVAL with a message
+ * and launch nothing.  The first call on each device looks up the scratch
+ * address with that device current, so make it before any stream capture.
+ * All calls share the one scratch array: calls that may overlap on the GPU
+ * (different streams without ordering) race and give wrong results.
+ * Errors: EINVAL (null pointer, sizes), ECUDA. */
+int fedbm_mass_noalloc(const double* f, const double* jac, const double* mass_colsum,
+                       int64_t K, int32_t Np, int32_t Q, double* total, int32_t* status,
+                       void* cuda_stream);
+
 const char* fedbm_last_error(void);
 
 #ifdef __cplusplus

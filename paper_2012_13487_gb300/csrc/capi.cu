@@ -257,6 +257,9 @@ int grid_for(int64_t n, int block) {
 }
 
 }  // namespace
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 }  // namespace fedbm
 
 using namespace fedbm;

@@ -80,6 +80,8 @@ SIGNATURES = {
     "fedbm_mass": (ctypes.c_int, [_P, _D]),
     "fedbm_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "fedbm_last_error": (ctypes.c_char_p, []),
+    "fedbm_mass_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                          _P, _P, _P]),
 }
 
 _lib = None
@@ -234,6 +236,12 @@ def fedbm_info(h):
     info = Info()
     _check(lib().fedbm_info(h, ctypes.byref(info)))
     return info
+
+
+def fedbm_mass_noalloc(f, jac, mass_colsum, K, Np, Q, total, status, stream=0):
+    """Allocation-free mass diagnostic on caller-owned device buffers (see the C header)."""
+    _check(lib().fedbm_mass_noalloc(_ptr(f), _ptr(jac), _ptr(mass_colsum), K, Np, Q, _ptr(total),
+                                    _ptr(status), ctypes.c_void_p(stream)))
 
 
 class Solver:
