@@ -159,7 +159,7 @@ class ClockSampler:
                                                     if r[3].replace(".", "").isdigit()) if rows else None}
 
 
-def make_solver(w, stream_handle, epc=0, tpb=0):
+def make_solver(w, stream_handle, epc=0, tpb=0, stages=0):
     from paper_2012_13487_gb300 import fedbm as fb
     if w["kind"] == "cavity":
         bc = (fb.BC_WALL_DIFFUSE,) * 4
@@ -171,7 +171,7 @@ def make_solver(w, stream_handle, epc=0, tpb=0):
     kind, n = w["vel"]
     v = fb.velset_desc(fb.VELSET_GH if kind == "gh" else fb.VELSET_NC, n, eq_order=w.get("eq_order", 2))
     prm = fb.params(kn=w["kn"], precision=PREC[w["precision"]], reduction=RED[w.get("reduction", "default")],
-                    cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb)
+                    cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb, pipeline_stages=stages)
     return fb.Solver(m, v, prm, stream_handle)
 
 
@@ -265,7 +265,7 @@ def run_ours(args, w, name):
     st = torch.cuda.Stream()
     K, Np, Q = dims(w)
     dof = K * Np * Q
-    s = make_solver(w, st.cuda_stream, args.epc, args.tpb)
+    s = make_solver(w, st.cuda_stream, args.epc, args.tpb, args.stages)
     s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
     s.step(args.warmup)
     torch.cuda.synchronize()
@@ -345,7 +345,8 @@ def run_ours(args, w, name):
             "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-state/f32", "fp16": "f16-state/f32"}[w["precision"]],
             "data": "synthetic",
             "config": {"workload": w["desc"], "name": name, "K": K, "Np": Np, "Q": Q, "dof": dof,
-                       "tile": {"elems_per_cta": s.info.elems_per_cta, "threads_per_cta": s.info.threads_per_cta},
+                       "tile": {"elems_per_cta": s.info.elems_per_cta, "threads_per_cta": s.info.threads_per_cta,
+                                "pipeline_stages": s.info.pipeline_stages, "grid": s.info.grid},
                        "l2": "inputs larger than L2 (state x2 + residual = %.0f MB), no flush" %
                              (dof * (2 * STATE_BYTES[w["precision"]] + RES_BYTES[w["precision"]]) / 1e6),
                        "parallelism": "replicas x%d" % world},
@@ -379,6 +380,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--epc", type=int, default=0, help="stage tile: elements per CTA (0 = library default)")
     ap.add_argument("--tpb", type=int, default=0, help="stage tile: threads per CTA (0 = library default)")
+    ap.add_argument("--stages", type=int, default=0, help="stage tile buffers per CTA (0 = library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

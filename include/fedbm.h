@@ -107,6 +107,8 @@ typedef struct fedbm_params {
   int32_t elems_per_cta; /* stage-kernel tile: elements per CTA (0 = auto)      */
   int32_t threads_per_cta; /* stage-kernel tile: threads per CTA, multiple of 32,
                             <= 256 (0 = auto)                                  */
+  int32_t pipeline_stages; /* stage-kernel tile buffers per CTA: 1, or 2 to load
+                              the next tile while computing one (0 = auto = 1) */
 } fedbm_params;
 
 typedef struct fedbm_info_t {
@@ -115,6 +117,8 @@ typedef struct fedbm_info_t {
   int64_t steps;                 /* completed RK steps                           */
   int32_t precision, reduction, order, eq_order;
   int32_t elems_per_cta, threads_per_cta;
+  int32_t pipeline_stages, grid; /* stage-kernel buffers per CTA; persistent grid */
+  int32_t group, ngroups;        /* batches: kernel group of this case; group count */
   int64_t state_bytes;           /* device bytes of one state buffer             */
   int64_t residual_bytes;        /* device bytes of the RK residual              */
 } fedbm_info_t;
@@ -198,6 +202,45 @@ int fedbm_get_residual(fedbm_solver* s, double* res, int32_t on_device);
 int fedbm_mass(fedbm_solver* s, double* total_mass);
 
 int fedbm_info(const fedbm_solver* s, fedbm_info_t* info);
+
+/* ---- batched form -------------------------------------------------------- */
+/* Many independent cases (each its own mesh, Kn, wall speeds, time step) that
+ * advance together (SURVEY batched form; the paper's Couette and cavity cases
+ * of Sec. III).  Cases with the same degree, velocity set, precision,
+ * reduction, collision switch, beta and tile parameters form one group: their
+ * element lists are concatenated and one stage-kernel launch per RK stage
+ * covers them all (per-element time step and 1/tau, per-case wall slots);
+ * groups are independent branches of one CUDA graph per RK step.  Every case
+ * takes one step of its own dt per fedbm_batch_rk_step step.  Case indices
+ * follow the order of `cases`. */
+typedef struct fedbm_case_desc {
+  fedbm_mesh_desc   mesh;
+  fedbm_velset_desc velset;
+  fedbm_params      params;
+} fedbm_case_desc;
+
+typedef struct fedbm_batch fedbm_batch;     /* opaque, library-owned */
+
+/* Set up every case (as fedbm_create does for one).  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+int fedbm_batch_create(const fedbm_case_desc* cases, int32_t ncases, void* cuda_stream,
+                       fedbm_batch** out);
+void fedbm_batch_destroy(fedbm_batch* b);
+/* Per-case counterparts of the solver calls (case c, 0 <= c < ncases). */
+int fedbm_batch_set_state(fedbm_batch* b, int32_t c, const double* f, int32_t on_device);
+int fedbm_batch_set_equilibrium(fedbm_batch* b, int32_t c, double rho0, double ux0, double uy0,
+                                double amp, uint64_t seed);
+int fedbm_batch_get_state(fedbm_batch* b, int32_t c, double* f, int32_t on_device);
+int fedbm_batch_get_moments(fedbm_batch* b, int32_t c, double* rho, double* ux, double* uy,
+                            int32_t on_device);
+int fedbm_batch_mass(fedbm_batch* b, int32_t c, double* total_mass);
+int fedbm_batch_info(const fedbm_batch* b, int32_t c, fedbm_info_t* info);
+/* Advance every case nsteps LSRK(5,4) steps (one graph launch per step). */
+int fedbm_batch_rk_step(fedbm_batch* b, int32_t nsteps);
+/* Re-tile one group's stage kernel (0 = automatic for each argument); used by
+ * the tile autotuner.  Takes effect from the next step. */
+int fedbm_batch_set_tiles(fedbm_batch* b, int32_t group, int32_t elems_per_cta,
+                          int32_t threads_per_cta, int32_t pipeline_stages);
 
 /* Allocation-free mass diagnostic.  The paper has no counterpart; this entry
  * point serves callers that must not allocate device memory once they are

@@ -25,6 +25,8 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+const char* g_last_error_c() { return g_last_error.c_str(); }
+
 #define FEDBM_CK(call)                                                                   \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \
@@ -256,115 +258,188 @@ int grid_for(int64_t n, int block) {
   return int(std::min<int64_t>((n + block - 1) / block, 152 * 32));
 }
 
-}  // namespace
 
-void set_last_error(const std::string& msg) { g_last_error = msg; }
 
-}  // namespace fedbm
+// ---------------------------------------------------------------- batch and solver objects
 
-using namespace fedbm;
-
-// ---------------------------------------------------------------- solver object
-struct fedbm_solver {
-  int device = 0;
-  cudaStream_t stream = nullptr;     // caller's stream
-  cudaStream_t capture = nullptr;    // private stream for graph capture
-  fedbm_mesh_desc mesh_desc{};
-  fedbm_velset_desc vs_desc{};
+// One case: its descriptors, its element range inside its group and its clock.
+struct Case {
+  fedbm_mesh_desc md{};
+  fedbm_velset_desc vd{};
   fedbm_params prm{};
-  Mesh mesh;
-  VelocitySet vs;
-  RefOps ops;
-  int store = kStoreF32;
+  int group = 0;
+  int local = 0;        // index of the case inside its group (wall slots 4*local .. 4*local+3)
+  int64_t k_off = 0;    // first element inside the group
   int64_t K = 0;
-  int Np = 0, Nfp = 0, Q = 0, Qp = 0;
-  int epc = 0, tpb = 0;
+  double dt = 0, tau = 0;
+};
+
+// Cases that share degree, velocity set, precision and kernel options run as
+// one concatenated element list: one stage-kernel launch covers all of them.
+struct Group {
+  int p = 0, store = kStoreF32, Q = 0, Qp = 0, Np = 0, Nfp = 0;
+  fedbm_velset_desc vd{};
+  int collision = 1, reduction = 0;
+  double beta = 1.0;
+  int64_t K = 0;
+  std::vector<int> cases;
+  int epc = 0, tpb = 0, nstages = 1, grid = 0;
   size_t smem = 0;
-  double dt = 0, tau = 0, time = 0;
-  int64_t steps = 0;
-  int cur = 0;                       // state buffer holding the current f
-  // device memory
+  RefOps ops;
+  VelocitySet vs;
   void* f[2] = {nullptr, nullptr};
   void* res = nullptr;
   float* scale[2] = {nullptr, nullptr};
   int32_t* nbr = nullptr;
-  void* geo = nullptr;               // [K][16] in the compute precision
-  void* vel = nullptr;               // [kVelRows][Qp] in the compute precision
-  double* vel64 = nullptr;           // [3][Qp] ex, ey, w in FP64
-  void* wall_feq = nullptr;          // [4][Qp]
-  void* wall_den_inv = nullptr;      // [4]
-  double* Jk = nullptr;              // [K]
-  double* mw = nullptr;              // [Np] column sums of M
-  double* staging = nullptr;         // canonical FP64 [K][Np][Q] (lazy)
-  double* mom = nullptr;             // [3][K][Np] (lazy)
-  double* partial = nullptr;         // [kMassBlocks + 1]
-  int* flag = nullptr;               // [0]: mass diagnostic flag, [1]: stage-kernel wait timeout
-  int wall_diffuse_mask = 0;
+  void* geo = nullptr;          // [K][16] compute precision
+  void* vel = nullptr;          // [kVelRows][Qp]
+  double* vel64 = nullptr;      // [3][Qp]
+  void* wall_feq = nullptr;     // [4 * ncases][Qp]
+  void* wall_den_inv = nullptr; // [4 * ncases]
+  double* Jk = nullptr;         // [K]
+  double* mw = nullptr;         // [Np]
+  double* partial = nullptr;    // mass partial sums [kMassBlocks + 1]
+  int* flag = nullptr;          // [0] mass diagnostic, [1] stage-kernel wait timeout
+  int wall_any = 0;
   double W0 = 0, W1x = 0, W1y = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t branch = nullptr;  // graph-capture branch of this group
 };
 
-namespace {
+struct Batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;
+  std::vector<Case> cases;
+  std::vector<Group> groups;
+  int cur = 0;                   // state buffer holding the current f (all groups step together)
+  double time = 0;               // RK steps taken since the last state load
+  int64_t steps = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  double* staging = nullptr;     // canonical FP64 buffer of the largest case (lazy)
+  size_t staging_elems = 0;
+  double* mom = nullptr;         // [3][K*Np] of the largest case (lazy)
+  size_t mom_elems = 0;
+};
+
+bool same_group(const Group& g, const fedbm_mesh_desc& md, const fedbm_velset_desc& vd, const fedbm_params& prm) {
+  return g.p == md.order && g.store == prm.precision && g.vd.kind == vd.kind && g.vd.n == vd.n &&
+         g.vd.nc_extent == vd.nc_extent && g.vd.nc_sqrt2 == vd.nc_sqrt2 && g.vd.eq_order == vd.eq_order &&
+         g.collision == prm.collision && g.reduction == prm.reduction && g.beta == prm.beta &&
+         g.epc == prm.elems_per_cta && g.tpb == prm.threads_per_cta && g.nstages == prm.pipeline_stages;
+}
 
 template <typename R>
-void fill_stage_args(const fedbm_solver* s, int stage, int from, StageArgs<R>& a) {
-  a.f_in = s->f[from];
-  a.f_out = s->f[1 - from];
-  a.res = static_cast<R*>(s->res);
-  a.scale_in = s->scale[from];
-  a.scale_out = s->scale[1 - from];
-  a.nbr = s->nbr;
-  a.geo = static_cast<const R*>(s->geo);
-  a.vel = static_cast<const R*>(s->vel);
-  a.wall_feq = static_cast<const R*>(s->wall_feq);
-  a.wall_den_inv = static_cast<const R*>(s->wall_den_inv);
-  a.wall_diffuse_mask = s->wall_diffuse_mask;
-  a.W0 = R(s->W0);
-  a.W1x = R(s->W1x);
-  a.W1y = R(s->W1y);
-  a.K = s->K;
-  a.Qp = s->Qp;
-  a.epc = s->epc;
-  a.dt = R(s->dt);
+void fill_stage_args(const Group& g, int stage, int from, StageArgs<R>& a) {
+  a.f_in = g.f[from];
+  a.f_out = g.f[1 - from];
+  a.res = static_cast<R*>(g.res);
+  a.scale_in = g.scale[from];
+  a.scale_out = g.scale[1 - from];
+  a.nbr = g.nbr;
+  a.geo = static_cast<const R*>(g.geo);
+  a.vel = static_cast<const R*>(g.vel);
+  a.wall_feq = static_cast<const R*>(g.wall_feq);
+  a.wall_den_inv = static_cast<const R*>(g.wall_den_inv);
+  a.wall_any = g.wall_any;
+  a.W0 = R(g.W0);
+  a.W1x = R(g.W1x);
+  a.W1y = R(g.W1y);
+  a.K = g.K;
+  a.Qp = g.Qp;
+  a.epc = g.epc;
+  a.nstages = g.nstages;
   a.rkA = R(kRkA[stage]);
   a.rkB = R(kRkB[stage]);
-  a.inv_tau = R(1.0 / s->tau);
-  a.ab = R(2.0 * s->prm.beta - 1.0);
-  a.collision = s->prm.collision;
-  a.eq_order = s->vs_desc.eq_order;
-  a.red = s->prm.reduction;
-  a.err = s->flag + 1;
+  a.ab = R(2.0 * g.beta - 1.0);
+  a.collision = g.collision;
+  a.eq_order = g.vd.eq_order;
+  a.red = g.reduction;
+  a.err = g.flag + 1;
 }
 
-cudaError_t launch_stage(const fedbm_solver* s, int stage, int from, cudaStream_t st) {
-  const int grid = int((s->K + s->epc - 1) / s->epc);
-  const StageEntry e = stage_entry(s->ops.p);
-  if (s->store == kStoreF64) {
+cudaError_t launch_stage(const Group& g, int stage, int from, cudaStream_t st) {
+  const StageEntry e = stage_entry(g.p);
+  if (g.store == kStoreF64) {
     StageArgs<double> a;
-    fill_stage_args(s, stage, from, a);
-    return e.launch(s->store, &a, grid, s->tpb, s->smem, st);
+    fill_stage_args(g, stage, from, a);
+    return e.launch(g.store, &a, g.grid, g.tpb, g.smem, st);
   }
   StageArgs<float> a;
-  fill_stage_args(s, stage, from, a);
-  return e.launch(s->store, &a, grid, s->tpb, s->smem, st);
+  fill_stage_args(g, stage, from, a);
+  return e.launch(g.store, &a, g.grid, g.tpb, g.smem, st);
 }
 
-int build_graphs(fedbm_solver* s) {
-  for (int c = 0; c < 2; ++c) {
-    if (s->graph[c]) continue;
-    cudaGraph_t g = nullptr;
-    FEDBM_CK(cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal));
-    int from = c;
-    cudaError_t le = cudaSuccess;
-    for (int st = 0; st < 5 && le == cudaSuccess; ++st) {
-      le = launch_stage(s, st, from, s->capture);
-      from = 1 - from;
+// Tile shape, pipeline depth and persistent grid of a group's stage kernel.
+int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
+  g.epc = epc > 0 ? epc : (g.Qp < 128 ? std::max(1, 128 / g.Qp) : 1);
+  g.tpb = tpb > 0 ? tpb : std::min(128, std::max(32, (g.epc * g.Qp + 31) / 32 * 32));
+  if (g.tpb % 32 || g.tpb > 256) return fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256");
+  if (stages < 0 || stages > 2) return fail(FEDBM_EINVAL, "pipeline_stages must be 0, 1 or 2");
+  g.nstages = stages == 2 ? 2 : 1;
+  g.smem = stage_smem_bytes(g.p, g.store, g.epc, g.Qp, g.nstages);
+  if (g.smem > 227 * 1024 && g.nstages == 2) {
+    g.nstages = 1;
+    g.smem = stage_smem_bytes(g.p, g.store, g.epc, g.Qp, 1);
+  }
+  if (g.smem > 227 * 1024) return fail(FEDBM_EINVAL, "stage tile does not fit in shared memory");
+  const StageEntry e = stage_entry(g.p);
+  FEDBM_CK(e.set_smem(g.store, g.Qp, g.smem));
+  int nsm = 0;
+  FEDBM_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device));
+  const int per_sm = e.occupancy(g.store, g.Qp, g.tpb, g.smem);
+  if (per_sm < 1) return fail(FEDBM_EINVAL, "stage tile cannot be resident on an SM");
+  const int64_t ntiles = (g.K + g.epc - 1) / g.epc;
+  g.grid = int(std::min<int64_t>(ntiles, int64_t(per_sm) * nsm));
+  for (int c = 0; c < 2; ++c)
+    if (b.graph[c]) {
+      cudaGraphExecDestroy(b.graph[c]);
+      b.graph[c] = nullptr;
     }
-    cudaError_t ee = cudaStreamEndCapture(s->capture, &g);
+  return FEDBM_OK;
+}
+
+// One RK step of every group, captured once per buffer parity; groups are
+// independent branches of the graph so that small groups run side by side.
+int build_graphs(Batch& b) {
+  for (int c = 0; c < 2; ++c) {
+    if (b.graph[c]) continue;
+    cudaGraph_t graph = nullptr;
+    FEDBM_CK(cudaStreamBeginCapture(b.capture, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    std::vector<cudaEvent_t> evs;
+    cudaEvent_t fork = nullptr;
+    const bool branches = b.groups.size() > 1;
+    if (branches) {
+      le = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+      if (le == cudaSuccess) le = cudaEventRecord(fork, b.capture);
+    }
+    for (Group& g : b.groups) {
+      if (le != cudaSuccess) break;
+      cudaStream_t st = b.capture;
+      if (branches) {
+        st = g.branch;
+        le = cudaStreamWaitEvent(st, fork, 0);
+      }
+      int from = c;
+      for (int s = 0; s < 5 && le == cudaSuccess; ++s) {
+        le = launch_stage(g, s, from, st);
+        from = 1 - from;
+      }
+      if (branches && le == cudaSuccess) {
+        cudaEvent_t done = nullptr;
+        le = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+        if (le == cudaSuccess) le = cudaEventRecord(done, st);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(b.capture, done, 0);
+        evs.push_back(done);
+      }
+    }
+    cudaError_t ee = cudaStreamEndCapture(b.capture, &graph);
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
     if (le != cudaSuccess) return fail(FEDBM_ECUDA, std::string("stage launch in capture: ") + cudaGetErrorString(le));
     if (ee != cudaSuccess) return fail(FEDBM_ECUDA, std::string("end capture: ") + cudaGetErrorString(ee));
-    cudaError_t ie = cudaGraphInstantiate(&s->graph[c], g, 0);
-    cudaGraphDestroy(g);
+    cudaError_t ie = cudaGraphInstantiate(&b.graph[c], graph, 0);
+    cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return fail(FEDBM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
   }
   return FEDBM_OK;
@@ -383,35 +458,455 @@ int upload_real(const std::vector<double>& h, void** d) {
   return upload_vec(v, d);
 }
 
-int ensure_staging(fedbm_solver* s) {
-  if (!s->staging) FEDBM_CK(cudaMalloc(&s->staging, size_t(s->K) * s->Np * s->Q * sizeof(double)));
+// Host set-up of a group in FP64 (meshes, walls, geometry) and device upload.
+int build_group(Batch& b, Group& g) {
+  std::string err;
+  if (!build_velocity_set(g.vd, g.vs, err)) return fail(FEDBM_EINVAL, err);
+  if (!build_ref_ops(g.p, g.ops, err)) return fail(FEDBM_EINVAL, err);
+  g.Np = g.ops.Np;
+  g.Nfp = g.ops.Nfp;
+  g.Q = g.vs.Q;
+  g.Qp = (g.Q + 7) / 8 * 8;
+  const int Np = g.Np, Qp = g.Qp, Q = g.Q;
+  const int nslots = 4 * int(g.cases.size());
+  std::vector<int32_t> nbr;
+  std::vector<double> geo, Jk, wfeq(size_t(nslots) * Qp, 0.0), wden(nslots, 0.0);
+  const double nrm[4][2] = {{0, -1}, {1, 0}, {0, 1}, {-1, 0}};
+  for (int lc = 0; lc < int(g.cases.size()); ++lc) {
+    Case& cs = b.cases[g.cases[lc]];
+    Mesh m;
+    if (!build_mesh(cs.md, m, err)) return fail(FEDBM_EINVAL, err);
+    cs.local = lc;
+    cs.k_off = g.K;
+    cs.K = m.K;
+    const double L = cs.prm.length > 0 ? cs.prm.length : 1.0;
+    cs.tau = cs.prm.kn * L / std::sqrt(3.0);
+    cs.dt = cs.prm.dt > 0 ? cs.prm.dt : time_step(m, g.vs, g.p, cs.prm.cfl);
+    const double itau = g.collision ? 1.0 / cs.tau : 0.0;
+    for (int64_t k = 0; k < m.K; ++k) {
+      for (int f = 0; f < 3; ++f) {
+        const int32_t code = m.nbr[k * 3 + f];
+        nbr.push_back(code >= 0 ? encode_face((code >> 3) + cs.k_off, (code >> 1) & 3, code & 1)
+                                : int32_t(-(4 * lc + (-code - 1) + 1)));
+      }
+      for (int j = 0; j < kGeoStride; ++j) geo.push_back(m.geo[k * kGeoStride + j]);
+      geo[geo.size() - kGeoStride + kGeoDt] = cs.dt;
+      geo[geo.size() - kGeoStride + kGeoInvTau] = itau;
+      Jk.push_back(m.geo[k * kGeoStride + kGeoJ]);
+    }
+    for (int sd = 0; sd < 4; ++sd) {
+      const int slot = 4 * lc + sd;
+      double den = 0.0;
+      for (int i = 0; i < Q; ++i) {
+        const double fb = equilibrium(g.vs.w[i], g.vs.ex[i], g.vs.ey[i], 1.0, cs.md.wall_ux[sd], cs.md.wall_uy[sd],
+                                      g.vd.eq_order);
+        wfeq[size_t(slot) * Qp + i] = fb;
+        const double en = g.vs.ex[i] * nrm[sd][0] + g.vs.ey[i] * nrm[sd][1];
+        if (en < 0) den -= en * fb;
+      }
+      if (cs.md.bc[sd] == FEDBM_BC_WALL_DIFFUSE && den > 0) {
+        wden[slot] = 1.0 / den;
+        g.wall_any = 1;
+      }
+    }
+    g.K += m.K;
+  }
+  // velocity table, padded with zero-weight zero-speed velocities
+  std::vector<double> vel(size_t(kVelRows) * Qp, 0.0), v64(size_t(3) * Qp, 0.0), mw(Np, 0.0);
+  for (int i = 0; i < Q; ++i) {
+    vel[kVelEx * Qp + i] = g.vs.ex[i];
+    vel[kVelEy * Qp + i] = g.vs.ey[i];
+    vel[kVelW * Qp + i] = g.vs.w[i];
+    vel[kVelInvW * Qp + i] = g.vs.w[i] > 0 ? 1.0 / g.vs.w[i] : 0.0;
+    vel[kVelWex * Qp + i] = g.vs.w[i] * g.vs.ex[i];
+    vel[kVelWey * Qp + i] = g.vs.w[i] * g.vs.ey[i];
+    v64[i] = g.vs.ex[i];
+    v64[Qp + i] = g.vs.ey[i];
+    v64[2 * Qp + i] = g.vs.w[i];
+    g.W0 += g.vs.w[i];
+    g.W1x += g.vs.w[i] * g.vs.ex[i];
+    g.W1y += g.vs.w[i] * g.vs.ey[i];
+  }
+  for (int j = 0; j < Np; ++j)
+    for (int n = 0; n < Np; ++n) mw[n] += g.ops.M[size_t(j) * Np + n];
+  const size_t dofp = size_t(g.K) * Np * Qp;
+  for (int c = 0; c < 2; ++c) {
+    FEDBM_CK(cudaMalloc(&g.f[c], dofp * store_bytes(g.store)));
+    FEDBM_CK(cudaMemset(g.f[c], 0, dofp * store_bytes(g.store)));
+    if (g.store >= kStoreBF16) {
+      FEDBM_CK(cudaMalloc(&g.scale[c], size_t(g.K) * sizeof(float)));
+      FEDBM_CK(cudaMemset(g.scale[c], 0, size_t(g.K) * sizeof(float)));
+    }
+  }
+  FEDBM_CK(cudaMalloc(&g.res, dofp * real_bytes(g.store)));
+  FEDBM_CK(cudaMemset(g.res, 0, dofp * real_bytes(g.store)));
+  int rc;
+  if ((rc = upload_vec(nbr, reinterpret_cast<void**>(&g.nbr))) != FEDBM_OK) return rc;
+  if ((rc = upload_vec(v64, reinterpret_cast<void**>(&g.vel64))) != FEDBM_OK) return rc;
+  if ((rc = upload_vec(Jk, reinterpret_cast<void**>(&g.Jk))) != FEDBM_OK) return rc;
+  if ((rc = upload_vec(mw, reinterpret_cast<void**>(&g.mw))) != FEDBM_OK) return rc;
+  if (g.store == kStoreF64) {
+    if ((rc = upload_real<double>(geo, &g.geo)) != FEDBM_OK) return rc;
+    if ((rc = upload_real<double>(vel, &g.vel)) != FEDBM_OK) return rc;
+    if ((rc = upload_real<double>(wfeq, &g.wall_feq)) != FEDBM_OK) return rc;
+    if ((rc = upload_real<double>(wden, &g.wall_den_inv)) != FEDBM_OK) return rc;
+  } else {
+    if ((rc = upload_real<float>(geo, &g.geo)) != FEDBM_OK) return rc;
+    if ((rc = upload_real<float>(vel, &g.vel)) != FEDBM_OK) return rc;
+    if ((rc = upload_real<float>(wfeq, &g.wall_feq)) != FEDBM_OK) return rc;
+    if ((rc = upload_real<float>(wden, &g.wall_den_inv)) != FEDBM_OK) return rc;
+  }
+  FEDBM_CK(cudaMalloc(&g.partial, (kMassBlocks + 1) * sizeof(double)));
+  FEDBM_CK(cudaMalloc(&g.flag, 2 * sizeof(int)));
+  FEDBM_CK(cudaMemset(g.flag, 0, 2 * sizeof(int)));
+  FEDBM_CK(cudaStreamCreateWithFlags(&g.branch, cudaStreamNonBlocking));
   return FEDBM_OK;
 }
 
-int encode_from_staging(fedbm_solver* s) {
-  const int b = 256;
-  switch (s->store) {
-    case kStoreF64: encode_kernel<StoreF64><<<int(s->K), b, 0, s->stream>>>(s->staging, s->f[s->cur], nullptr, s->vel64, s->Np, s->Q, s->Qp); break;
-    case kStoreF32: encode_kernel<StoreF32><<<int(s->K), b, 0, s->stream>>>(s->staging, s->f[s->cur], nullptr, s->vel64, s->Np, s->Q, s->Qp); break;
-    case kStoreBF16: encode_kernel<StoreBF16><<<int(s->K), b, 0, s->stream>>>(s->staging, s->f[s->cur], s->scale[s->cur], s->vel64, s->Np, s->Q, s->Qp); break;
-    default: encode_kernel<StoreF16><<<int(s->K), b, 0, s->stream>>>(s->staging, s->f[s->cur], s->scale[s->cur], s->vel64, s->Np, s->Q, s->Qp); break;
+void free_batch(Batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int c = 0; c < 2; ++c)
+    if (b->graph[c]) cudaGraphExecDestroy(b->graph[c]);
+  for (Group& g : b->groups) {
+    for (int c = 0; c < 2; ++c) {
+      cudaFree(g.f[c]);
+      cudaFree(g.scale[c]);
+    }
+    void* bufs[] = {g.res, g.nbr, g.geo, g.vel, g.vel64, g.wall_feq, g.wall_den_inv, g.Jk, g.mw, g.partial, g.flag};
+    for (void* p : bufs) cudaFree(p);
+    if (g.branch) cudaStreamDestroy(g.branch);
+  }
+  cudaFree(b->staging);
+  cudaFree(b->mom);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+}
+
+int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** out) {
+  if (!cd || ncases < 1 || !out) return fail(FEDBM_EINVAL, "need at least one case and an output pointer");
+  *out = nullptr;
+  Batch* b = new Batch();
+  b->stream = static_cast<cudaStream_t>(stream);
+  auto bail = [&](int code) {
+    free_batch(b);
+    return code;
+  };
+  for (int c = 0; c < ncases; ++c) {
+    const fedbm_params& prm = cd[c].params;
+    if (prm.precision < FEDBM_FP64 || prm.precision > FEDBM_FP16_DEV) return bail(fail(FEDBM_EINVAL, "unknown precision"));
+    if (prm.reduction < FEDBM_RED_DEFAULT || prm.reduction > FEDBM_RED_COMP_FP32)
+      return bail(fail(FEDBM_EINVAL, "unknown reduction mode"));
+    if (!(prm.kn > 0)) return bail(fail(FEDBM_EINVAL, "kn must be > 0"));
+    if (!(prm.beta >= 0.5 && prm.beta <= 1.0)) return bail(fail(FEDBM_EINVAL, "beta must be in [0.5, 1]"));
+    if (!(prm.dt > 0) && !(prm.cfl > 0)) return bail(fail(FEDBM_EINVAL, "need dt > 0 or cfl > 0"));
+    if (cd[c].mesh.order < 0 || cd[c].mesh.order > kMaxOrder) return bail(fail(FEDBM_EINVAL, "order must be in 0..6"));
+    Case cs;
+    cs.md = cd[c].mesh;
+    cs.vd = cd[c].velset;
+    cs.prm = prm;
+    int gi = -1;
+    for (int j = 0; j < int(b->groups.size()); ++j)
+      if (same_group(b->groups[j], cs.md, cs.vd, cs.prm)) gi = j;
+    if (gi < 0) {
+      Group g;
+      g.p = cs.md.order;
+      g.store = prm.precision;
+      g.vd = cs.vd;
+      g.collision = prm.collision;
+      g.reduction = prm.reduction;
+      g.beta = prm.beta;
+      g.epc = prm.elems_per_cta;
+      g.tpb = prm.threads_per_cta;
+      g.nstages = prm.pipeline_stages;
+      b->groups.push_back(g);
+      gi = int(b->groups.size()) - 1;
+    }
+    cs.group = gi;
+    b->groups[gi].cases.push_back(c);
+    b->cases.push_back(cs);
+  }
+  int rc = FEDBM_OK;
+  if ((rc = [&]() -> int {
+         FEDBM_CK(cudaGetDevice(&b->device));
+         int r = ensure_ops_uploaded(b->device);
+         if (r != FEDBM_OK) return r;
+         FEDBM_CK(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
+         for (Group& g : b->groups) {
+           const int epc = g.epc, tpb = g.tpb, st = g.nstages;
+           if ((r = build_group(*b, g)) != FEDBM_OK) return r;
+           if ((r = configure_tiles(*b, g, epc, tpb, st)) != FEDBM_OK) return r;
+         }
+         return FEDBM_OK;
+       }()) != FEDBM_OK)
+    return bail(rc);
+  *out = b;
+  return FEDBM_OK;
+}
+
+int check_batch(const Batch* b, int c) {
+  if (!b) return fail(FEDBM_EINVAL, "null handle");
+  if (c < 0 || c >= int(b->cases.size())) return fail(FEDBM_EINVAL, "case index out of range");
+  FEDBM_CK(cudaSetDevice(b->device));
+  return FEDBM_OK;
+}
+
+int ensure_staging(Batch& b, size_t elems) {
+  if (b.staging_elems < elems) {
+    cudaFree(b.staging);
+    b.staging = nullptr;
+    b.staging_elems = 0;
+    FEDBM_CK(cudaMalloc(&b.staging, elems * sizeof(double)));
+    b.staging_elems = elems;
+  }
+  return FEDBM_OK;
+}
+
+// canonical FP64 (device) -> internal state of case c
+int encode_case(Batch& b, int c, const double* src) {
+  const Case& cs = b.cases[c];
+  const Group& g = b.groups[cs.group];
+  const size_t off = size_t(cs.k_off) * g.Np * g.Qp;
+  float* sc = g.scale[b.cur] ? g.scale[b.cur] + cs.k_off : nullptr;
+  const int blk = 256;
+  switch (g.store) {
+    case kStoreF64: encode_kernel<StoreF64><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<double*>(g.f[b.cur]) + off, nullptr, g.vel64, g.Np, g.Q, g.Qp); break;
+    case kStoreF32: encode_kernel<StoreF32><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<float*>(g.f[b.cur]) + off, nullptr, g.vel64, g.Np, g.Q, g.Qp); break;
+    case kStoreBF16: encode_kernel<StoreBF16><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__nv_bfloat16*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
+    default: encode_kernel<StoreF16><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__half*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
   }
   FEDBM_CK(cudaGetLastError());
-  s->time = 0;
-  s->steps = 0;
+  b.time = 0;
+  b.steps = 0;
   return FEDBM_OK;
 }
 
-int check_solver(const fedbm_solver* s) {
-  if (!s) return fail(FEDBM_EINVAL, "null solver");
-  FEDBM_CK(cudaSetDevice(s->device));
+int set_state(Batch& b, int c, const double* f, int on_device) {
+  if (!f) return fail(FEDBM_EINVAL, "null state pointer");
+  const Case& cs = b.cases[c];
+  const Group& g = b.groups[cs.group];
+  const size_t n = size_t(cs.K) * g.Np * g.Q;
+  const double* src = f;
+  if (!on_device) {
+    int rc = ensure_staging(b, n);
+    if (rc) return rc;
+    FEDBM_CK(cudaMemcpyAsync(b.staging, f, n * sizeof(double), cudaMemcpyHostToDevice, b.stream));
+    src = b.staging;
+  }
+  int rc = encode_case(b, c, src);
+  if (rc) return rc;
+  if (!on_device) FEDBM_CK(cudaStreamSynchronize(b.stream));
+  return FEDBM_OK;
+}
+
+int set_equilibrium(Batch& b, int c, double rho0, double ux0, double uy0, double amp, uint64_t seed) {
+  const Case& cs = b.cases[c];
+  const Group& g = b.groups[cs.group];
+  const int64_t n = cs.K * g.Np * g.Q;
+  int rc = ensure_staging(b, size_t(n));
+  if (rc) return rc;
+  equilibrium_kernel<<<grid_for(n, 256), 256, 0, b.stream>>>(b.staging, g.vel64, cs.K, g.Np, g.Q, g.Qp, rho0, ux0, uy0,
+                                                             amp, seed, g.vd.eq_order);
+  FEDBM_CK(cudaGetLastError());
+  return encode_case(b, c, b.staging);
+}
+
+template <class ST>
+void launch_decode(const Group& g, int cur, const Case& cs, double* dst, cudaStream_t st) {
+  using S = typename ST::S;
+  const int64_t n = cs.K * g.Np * g.Q;
+  const S* in = static_cast<const S*>(g.f[cur]) + size_t(cs.k_off) * g.Np * g.Qp;
+  const float* sc = g.scale[cur] ? g.scale[cur] + cs.k_off : nullptr;
+  decode_kernel<ST><<<grid_for(n, 256), 256, 0, st>>>(in, sc, dst, g.vel64, cs.K, g.Np, g.Q, g.Qp);
+}
+
+int get_state(Batch& b, int c, double* f, int on_device) {
+  if (!f) return fail(FEDBM_EINVAL, "null output");
+  const Case& cs = b.cases[c];
+  const Group& g = b.groups[cs.group];
+  const size_t n = size_t(cs.K) * g.Np * g.Q;
+  double* dst = f;
+  if (!on_device) {
+    int rc = ensure_staging(b, n);
+    if (rc) return rc;
+    dst = b.staging;
+  }
+  switch (g.store) {
+    case kStoreF64: launch_decode<StoreF64>(g, b.cur, cs, dst, b.stream); break;
+    case kStoreF32: launch_decode<StoreF32>(g, b.cur, cs, dst, b.stream); break;
+    case kStoreBF16: launch_decode<StoreBF16>(g, b.cur, cs, dst, b.stream); break;
+    default: launch_decode<StoreF16>(g, b.cur, cs, dst, b.stream); break;
+  }
+  FEDBM_CK(cudaGetLastError());
+  if (!on_device) {
+    FEDBM_CK(cudaMemcpyAsync(f, dst, n * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+    FEDBM_CK(cudaStreamSynchronize(b.stream));
+  }
+  return FEDBM_OK;
+}
+
+int get_residual(Batch& b, int c, double* r, int on_device) {
+  if (!r) return fail(FEDBM_EINVAL, "null output");
+  const Case& cs = b.cases[c];
+  const Group& g = b.groups[cs.group];
+  const int64_t n = cs.K * g.Np * g.Q;
+  double* dst = r;
+  if (!on_device) {
+    int rc = ensure_staging(b, size_t(n));
+    if (rc) return rc;
+    dst = b.staging;
+  }
+  const size_t off = size_t(cs.k_off) * g.Np * g.Qp;
+  if (g.store == kStoreF64)
+    decode_residual_kernel<double><<<grid_for(n, 256), 256, 0, b.stream>>>(static_cast<const double*>(g.res) + off, dst, cs.K, g.Np, g.Q, g.Qp);
+  else
+    decode_residual_kernel<float><<<grid_for(n, 256), 256, 0, b.stream>>>(static_cast<const float*>(g.res) + off, dst, cs.K, g.Np, g.Q, g.Qp);
+  FEDBM_CK(cudaGetLastError());
+  if (!on_device) {
+    FEDBM_CK(cudaMemcpyAsync(r, dst, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+    FEDBM_CK(cudaStreamSynchronize(b.stream));
+  }
+  return FEDBM_OK;
+}
+
+template <class ST>
+void launch_moments(const Group& g, int cur, const Case& cs, double* r, double* x, double* y, cudaStream_t st) {
+  using S = typename ST::S;
+  const int64_t nodes = cs.K * g.Np;
+  const S* in = static_cast<const S*>(g.f[cur]) + size_t(cs.k_off) * g.Np * g.Qp;
+  const float* sc = g.scale[cur] ? g.scale[cur] + cs.k_off : nullptr;
+  moments_kernel<ST><<<grid_for(nodes, 256), 256, 0, st>>>(in, sc, g.vel64, cs.K, g.Np, g.Qp, r, x, y);
+}
+
+int get_moments(Batch& b, int c, double* rho, double* ux, double* uy, int on_device) {
+  const Case& cs = b.cases[c];
+  const Group& g = b.groups[cs.group];
+  const int64_t nodes = cs.K * g.Np;
+  double *dr = rho, *dx = ux, *dy = uy;
+  if (!on_device) {
+    if (b.mom_elems < size_t(3 * nodes)) {
+      cudaFree(b.mom);
+      b.mom = nullptr;
+      b.mom_elems = 0;
+      FEDBM_CK(cudaMalloc(&b.mom, size_t(3) * nodes * sizeof(double)));
+      b.mom_elems = size_t(3) * nodes;
+    }
+    dr = b.mom;
+    dx = b.mom + nodes;
+    dy = b.mom + 2 * nodes;
+  } else if (!rho || !ux || !uy) {
+    return fail(FEDBM_EINVAL, "device moments need three output pointers");
+  }
+  switch (g.store) {
+    case kStoreF64: launch_moments<StoreF64>(g, b.cur, cs, dr, dx, dy, b.stream); break;
+    case kStoreF32: launch_moments<StoreF32>(g, b.cur, cs, dr, dx, dy, b.stream); break;
+    case kStoreBF16: launch_moments<StoreBF16>(g, b.cur, cs, dr, dx, dy, b.stream); break;
+    default: launch_moments<StoreF16>(g, b.cur, cs, dr, dx, dy, b.stream); break;
+  }
+  FEDBM_CK(cudaGetLastError());
+  if (!on_device) {
+    const size_t bytes = size_t(nodes) * sizeof(double);
+    if (rho) FEDBM_CK(cudaMemcpyAsync(rho, dr, bytes, cudaMemcpyDeviceToHost, b.stream));
+    if (ux) FEDBM_CK(cudaMemcpyAsync(ux, dx, bytes, cudaMemcpyDeviceToHost, b.stream));
+    if (uy) FEDBM_CK(cudaMemcpyAsync(uy, dy, bytes, cudaMemcpyDeviceToHost, b.stream));
+    FEDBM_CK(cudaStreamSynchronize(b.stream));
+  }
+  return FEDBM_OK;
+}
+
+template <class ST>
+void launch_mass(const Group& g, int cur, const Case& cs, int blocks, cudaStream_t st) {
+  using S = typename ST::S;
+  const S* in = static_cast<const S*>(g.f[cur]) + size_t(cs.k_off) * g.Np * g.Qp;
+  const float* sc = g.scale[cur] ? g.scale[cur] + cs.k_off : nullptr;
+  mass_partial_kernel<ST><<<blocks, kMassThreads, 0, st>>>(in, sc, g.vel64, g.Jk + cs.k_off, g.mw, cs.K, g.Np, g.Qp,
+                                                           g.partial, g.flag);
+}
+
+int mass(Batch& b, int c, double* total) {
+  if (!total) return fail(FEDBM_EINVAL, "null output");
+  const Case& cs = b.cases[c];
+  const Group& g = b.groups[cs.group];
+  FEDBM_CK(cudaMemsetAsync(g.flag, 0, sizeof(int), b.stream));
+  const int64_t nodes = cs.K * g.Np;
+  const int blocks = int(std::min<int64_t>(kMassBlocks, (nodes + kMassThreads - 1) / kMassThreads));
+  switch (g.store) {
+    case kStoreF64: launch_mass<StoreF64>(g, b.cur, cs, blocks, b.stream); break;
+    case kStoreF32: launch_mass<StoreF32>(g, b.cur, cs, blocks, b.stream); break;
+    case kStoreBF16: launch_mass<StoreBF16>(g, b.cur, cs, blocks, b.stream); break;
+    default: launch_mass<StoreF16>(g, b.cur, cs, blocks, b.stream); break;
+  }
+  FEDBM_CK(cudaGetLastError());
+  mass_final_kernel<<<1, 256, 0, b.stream>>>(g.partial, blocks, g.partial + kMassBlocks);
+  FEDBM_CK(cudaGetLastError());
+  int flag[2] = {0, 0};
+  FEDBM_CK(cudaMemcpyAsync(total, g.partial + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  FEDBM_CK(cudaMemcpyAsync(flag, g.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+  FEDBM_CK(cudaStreamSynchronize(b.stream));
+  if (flag[1]) return fail(FEDBM_ETIMEOUT, "a stage kernel's bounded wait for its tile copies gave up");
+  if (flag[0]) return fail(FEDBM_ENONFINITE, "state has a non-finite value or a node with rho <= 0");
+  return FEDBM_OK;
+}
+
+int rk_step(Batch& b, int nsteps) {
+  if (nsteps < 0) return fail(FEDBM_EINVAL, "nsteps must be >= 0");
+  int rc = build_graphs(b);
+  if (rc) return rc;
+  for (int n = 0; n < nsteps; ++n) {
+    FEDBM_CK(cudaGraphLaunch(b.graph[b.cur], b.stream));
+    b.cur = 1 - b.cur;  // five stages: the state ends in the other buffer
+    b.steps += 1;
+  }
+  return FEDBM_OK;
+}
+
+int info(const Batch& b, int c, fedbm_info_t* out) {
+  if (!out) return fail(FEDBM_EINVAL, "null output");
+  const Case& cs = b.cases[c];
+  const Group& g = b.groups[cs.group];
+  out->K = cs.K;
+  out->Np = g.Np;
+  out->Nfp = g.Nfp;
+  out->Q = g.Q;
+  out->Q_padded = g.Qp;
+  out->dt = cs.dt;
+  out->tau = cs.tau;
+  out->time = cs.dt * double(b.steps);
+  out->steps = b.steps;
+  out->precision = g.store;
+  out->reduction = g.reduction;
+  out->order = g.p;
+  out->eq_order = g.vd.eq_order;
+  out->elems_per_cta = g.epc;
+  out->threads_per_cta = g.tpb;
+  out->pipeline_stages = g.nstages;
+  out->grid = g.grid;
+  out->group = cs.group;
+  out->ngroups = int32_t(b.groups.size());
+  out->state_bytes = cs.K * g.Np * g.Qp * int64_t(store_bytes(g.store));
+  out->residual_bytes = cs.K * g.Np * g.Qp * int64_t(real_bytes(g.store));
   return FEDBM_OK;
 }
 
 }  // namespace
 
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace fedbm
+
+using namespace fedbm;
+
+// Opaque handles of the C ABI: a solver is a batch of one case.
+struct fedbm_batch {
+  Batch* b = nullptr;
+};
+struct fedbm_solver {
+  Batch* b = nullptr;
+};
+
 // ---------------------------------------------------------------- host-only queries
-extern "C" const char* fedbm_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char* fedbm_last_error(void) { return g_last_error_c(); }
 
 extern "C" int fedbm_velset(const fedbm_velset_desc* d, double* ex, double* ey, double* w, int32_t* q) {
   if (!d) return fail(FEDBM_EINVAL, "null descriptor");
@@ -475,319 +970,156 @@ extern "C" int fedbm_mesh_connectivity(const fedbm_mesh_desc* md, int32_t* nbr) 
   return FEDBM_OK;
 }
 
-// ---------------------------------------------------------------- lifecycle
-extern "C" void fedbm_destroy(fedbm_solver* s) {
-  if (!s) return;
-  cudaSetDevice(s->device);
-  if (s->stream) cudaStreamSynchronize(s->stream);
-  for (int c = 0; c < 2; ++c) {
-    if (s->graph[c]) cudaGraphExecDestroy(s->graph[c]);
-    cudaFree(s->f[c]);
-    cudaFree(s->scale[c]);
-  }
-  void* bufs[] = {s->res, s->nbr, s->geo, s->vel, s->vel64, s->wall_feq, s->wall_den_inv,
-                  s->Jk, s->mw, s->staging, s->mom, s->partial, s->flag};
-  for (void* b : bufs) cudaFree(b);
-  if (s->capture) cudaStreamDestroy(s->capture);
-  delete s;
-}
-
+// ---------------------------------------------------------------- single solver
 extern "C" int fedbm_create(const fedbm_mesh_desc* md, const fedbm_velset_desc* vd, const fedbm_params* prm,
                             void* cuda_stream, fedbm_solver** out) {
   if (!md || !vd || !prm || !out) return fail(FEDBM_EINVAL, "null argument");
   *out = nullptr;
+  fedbm_case_desc cd;
+  cd.mesh = *md;
+  cd.velset = *vd;
+  cd.params = *prm;
+  Batch* b = nullptr;
+  int rc = create_batch(&cd, 1, cuda_stream, &b);
+  if (rc) return rc;
   fedbm_solver* s = new fedbm_solver();
-  s->mesh_desc = *md;
-  s->vs_desc = *vd;
-  s->prm = *prm;
-  s->stream = static_cast<cudaStream_t>(cuda_stream);
-  int rc = FEDBM_OK;
-  auto bail = [&](int code) {
-    fedbm_destroy(s);
-    return code;
-  };
-  std::string err;
-  if (prm->precision < FEDBM_FP64 || prm->precision > FEDBM_FP16_DEV)
-    return bail(fail(FEDBM_EINVAL, "unknown precision"));
-  if (prm->reduction < FEDBM_RED_DEFAULT || prm->reduction > FEDBM_RED_COMP_FP32)
-    return bail(fail(FEDBM_EINVAL, "unknown reduction mode"));
-  if (!(prm->kn > 0)) return bail(fail(FEDBM_EINVAL, "kn must be > 0"));
-  if (!(prm->beta >= 0.5 && prm->beta <= 1.0)) return bail(fail(FEDBM_EINVAL, "beta must be in [0.5, 1]"));
-  if (!(prm->dt > 0) && !(prm->cfl > 0)) return bail(fail(FEDBM_EINVAL, "need dt > 0 or cfl > 0"));
-  if (!build_velocity_set(*vd, s->vs, err)) return bail(fail(FEDBM_EINVAL, err));
-  if (!build_mesh(*md, s->mesh, err)) return bail(fail(FEDBM_EINVAL, err));
-  if (!build_ref_ops(md->order, s->ops, err)) return bail(fail(FEDBM_EINVAL, err));
-  s->store = prm->precision;  // enum values coincide with StoreKind
-  s->K = s->mesh.K;
-  s->Np = s->ops.Np;
-  s->Nfp = s->ops.Nfp;
-  s->Q = s->vs.Q;
-  s->Qp = (s->Q + 7) / 8 * 8;
-  const double L = prm->length > 0 ? prm->length : 1.0;
-  s->tau = prm->kn * L / std::sqrt(3.0);
-  s->dt = prm->dt > 0 ? prm->dt : time_step(s->mesh, s->vs, md->order, prm->cfl);
-  // stage tile: elements per CTA and threads per CTA
-  s->epc = prm->elems_per_cta > 0 ? prm->elems_per_cta : (s->Qp < 128 ? std::max(1, 128 / s->Qp) : 1);
-  if (prm->threads_per_cta > 0) {
-    s->tpb = prm->threads_per_cta;
-  } else {
-    s->tpb = std::min(256, std::max(32, (s->epc * s->Qp + 31) / 32 * 32));
-  }
-  if (s->tpb % 32 || s->tpb > 256) return bail(fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256"));
-  s->smem = stage_smem_bytes(md->order, s->store, s->epc, s->Qp);
-  if (s->smem > 227 * 1024) return bail(fail(FEDBM_EINVAL, "stage tile does not fit in shared memory"));
-
-  if ((rc = [&]() -> int {
-         FEDBM_CK(cudaGetDevice(&s->device));
-         if ((rc = ensure_ops_uploaded(s->device)) != FEDBM_OK) return rc;
-         FEDBM_CK(cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking));
-         const StageEntry e = stage_entry(md->order);
-         FEDBM_CK(e.set_smem(s->store, s->smem));
-         const size_t dofp = size_t(s->K) * s->Np * s->Qp;
-         for (int c = 0; c < 2; ++c) {
-           FEDBM_CK(cudaMalloc(&s->f[c], dofp * store_bytes(s->store)));
-           FEDBM_CK(cudaMemset(s->f[c], 0, dofp * store_bytes(s->store)));
-           if (s->store >= kStoreBF16) {
-             FEDBM_CK(cudaMalloc(&s->scale[c], size_t(s->K) * sizeof(float)));
-             FEDBM_CK(cudaMemset(s->scale[c], 0, size_t(s->K) * sizeof(float)));
-           }
-         }
-         FEDBM_CK(cudaMalloc(&s->res, dofp * real_bytes(s->store)));
-         FEDBM_CK(cudaMemset(s->res, 0, dofp * real_bytes(s->store)));
-         // velocity table, padded with zero-weight zero-speed velocities
-         const int Qp = s->Qp, Q = s->Q;
-         std::vector<double> vel(size_t(kVelRows) * Qp, 0.0), v64(size_t(3) * Qp, 0.0);
-         for (int i = 0; i < Q; ++i) {
-           vel[kVelEx * Qp + i] = s->vs.ex[i];
-           vel[kVelEy * Qp + i] = s->vs.ey[i];
-           vel[kVelW * Qp + i] = s->vs.w[i];
-           vel[kVelInvW * Qp + i] = s->vs.w[i] > 0 ? 1.0 / s->vs.w[i] : 0.0;
-           vel[kVelWex * Qp + i] = s->vs.w[i] * s->vs.ex[i];
-           vel[kVelWey * Qp + i] = s->vs.w[i] * s->vs.ey[i];
-           v64[i] = s->vs.ex[i];
-           v64[Qp + i] = s->vs.ey[i];
-           v64[2 * Qp + i] = s->vs.w[i];
-           s->W0 += s->vs.w[i];
-           s->W1x += s->vs.w[i] * s->vs.ex[i];
-           s->W1y += s->vs.w[i] * s->vs.ey[i];
-         }
-         // walls: f^eq(1, u_b) per side and the eq. FullBC denominators
-         const double nrm[4][2] = {{0, -1}, {1, 0}, {0, 1}, {-1, 0}};
-         std::vector<double> wfeq(size_t(4) * Qp, 0.0), wden(4, 0.0);
-         for (int sd = 0; sd < 4; ++sd) {
-           if (md->bc[sd] == FEDBM_BC_WALL_DIFFUSE) s->wall_diffuse_mask |= 1 << sd;
-           double den = 0.0;
-           for (int i = 0; i < Q; ++i) {
-             const double fb = equilibrium(s->vs.w[i], s->vs.ex[i], s->vs.ey[i], 1.0, md->wall_ux[sd],
-                                           md->wall_uy[sd], vd->eq_order);
-             wfeq[size_t(sd) * Qp + i] = fb;
-             const double en = s->vs.ex[i] * nrm[sd][0] + s->vs.ey[i] * nrm[sd][1];
-             if (en < 0) den -= en * fb;
-           }
-           wden[sd] = den > 0 ? 1.0 / den : 0.0;
-         }
-         std::vector<double> Jk(s->K), mw(s->Np, 0.0);
-         for (int64_t k = 0; k < s->K; ++k) Jk[k] = s->mesh.geo[k * kGeoStride + 13];
-         for (int j = 0; j < s->Np; ++j)
-           for (int n = 0; n < s->Np; ++n) mw[n] += s->ops.M[size_t(j) * s->Np + n];
-         if ((rc = upload_vec(s->mesh.nbr, reinterpret_cast<void**>(&s->nbr))) != FEDBM_OK) return rc;
-         if ((rc = upload_vec(v64, reinterpret_cast<void**>(&s->vel64))) != FEDBM_OK) return rc;
-         if ((rc = upload_vec(Jk, reinterpret_cast<void**>(&s->Jk))) != FEDBM_OK) return rc;
-         if ((rc = upload_vec(mw, reinterpret_cast<void**>(&s->mw))) != FEDBM_OK) return rc;
-         if (s->store == kStoreF64) {
-           if ((rc = upload_real<double>(s->mesh.geo, &s->geo)) != FEDBM_OK) return rc;
-           if ((rc = upload_real<double>(vel, &s->vel)) != FEDBM_OK) return rc;
-           if ((rc = upload_real<double>(wfeq, &s->wall_feq)) != FEDBM_OK) return rc;
-           if ((rc = upload_real<double>(wden, &s->wall_den_inv)) != FEDBM_OK) return rc;
-         } else {
-           if ((rc = upload_real<float>(s->mesh.geo, &s->geo)) != FEDBM_OK) return rc;
-           if ((rc = upload_real<float>(vel, &s->vel)) != FEDBM_OK) return rc;
-           if ((rc = upload_real<float>(wfeq, &s->wall_feq)) != FEDBM_OK) return rc;
-           if ((rc = upload_real<float>(wden, &s->wall_den_inv)) != FEDBM_OK) return rc;
-         }
-         FEDBM_CK(cudaMalloc(&s->partial, (kMassBlocks + 1) * sizeof(double)));
-         FEDBM_CK(cudaMalloc(&s->flag, 2 * sizeof(int)));
-         FEDBM_CK(cudaMemset(s->flag, 0, 2 * sizeof(int)));
-         return FEDBM_OK;
-       }()) != FEDBM_OK)
-    return bail(rc);
+  s->b = b;
   *out = s;
   return FEDBM_OK;
 }
 
-// ---------------------------------------------------------------- state
+extern "C" void fedbm_destroy(fedbm_solver* s) {
+  if (!s) return;
+  free_batch(s->b);
+  delete s;
+}
+
+#define FEDBM_SOLVER(s)                                         \
+  if (!(s)) return fail(FEDBM_EINVAL, "null solver");            \
+  Batch& B = *(s)->b;                                           \
+  do {                                                          \
+    int rc_ = check_batch(&B, 0);                               \
+    if (rc_) return rc_;                                        \
+  } while (0)
+
 extern "C" int fedbm_set_state(fedbm_solver* s, const double* f, int32_t on_device) {
-  int rc = check_solver(s);
-  if (rc) return rc;
-  if (!f) return fail(FEDBM_EINVAL, "null state pointer");
-  if ((rc = ensure_staging(s))) return rc;
-  const size_t bytes = size_t(s->K) * s->Np * s->Q * sizeof(double);
-  FEDBM_CK(cudaMemcpyAsync(s->staging, f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                           s->stream));
-  if ((rc = encode_from_staging(s))) return rc;
-  if (!on_device) FEDBM_CK(cudaStreamSynchronize(s->stream));
-  return FEDBM_OK;
+  FEDBM_SOLVER(s);
+  return set_state(B, 0, f, on_device);
 }
 
 extern "C" int fedbm_set_equilibrium(fedbm_solver* s, double rho0, double ux0, double uy0, double amp,
                                      uint64_t seed) {
-  int rc = check_solver(s);
-  if (rc) return rc;
-  if ((rc = ensure_staging(s))) return rc;
-  const int64_t n = s->K * s->Np * s->Q;
-  equilibrium_kernel<<<grid_for(n, 256), 256, 0, s->stream>>>(s->staging, s->vel64, s->K, s->Np, s->Q, s->Qp, rho0,
-                                                              ux0, uy0, amp, seed, s->vs_desc.eq_order);
-  FEDBM_CK(cudaGetLastError());
-  return encode_from_staging(s);
+  FEDBM_SOLVER(s);
+  return set_equilibrium(B, 0, rho0, ux0, uy0, amp, seed);
 }
 
-extern "C" int fedbm_get_state(fedbm_solver* s, double* f, int32_t on_device) {
-  int rc = check_solver(s);
-  if (rc) return rc;
-  if (!f) return fail(FEDBM_EINVAL, "null output");
-  double* dst = f;
-  if (!on_device) {
-    if ((rc = ensure_staging(s))) return rc;
-    dst = s->staging;
-  }
-  const int64_t n = s->K * s->Np * s->Q;
-  const int g = grid_for(n, 256);
-  switch (s->store) {
-    case kStoreF64: decode_kernel<StoreF64><<<g, 256, 0, s->stream>>>(s->f[s->cur], nullptr, dst, s->vel64, s->K, s->Np, s->Q, s->Qp); break;
-    case kStoreF32: decode_kernel<StoreF32><<<g, 256, 0, s->stream>>>(s->f[s->cur], nullptr, dst, s->vel64, s->K, s->Np, s->Q, s->Qp); break;
-    case kStoreBF16: decode_kernel<StoreBF16><<<g, 256, 0, s->stream>>>(s->f[s->cur], s->scale[s->cur], dst, s->vel64, s->K, s->Np, s->Q, s->Qp); break;
-    default: decode_kernel<StoreF16><<<g, 256, 0, s->stream>>>(s->f[s->cur], s->scale[s->cur], dst, s->vel64, s->K, s->Np, s->Q, s->Qp); break;
-  }
-  FEDBM_CK(cudaGetLastError());
-  if (!on_device) {
-    FEDBM_CK(cudaMemcpyAsync(f, dst, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    FEDBM_CK(cudaStreamSynchronize(s->stream));
-  }
-  return FEDBM_OK;
-}
-
-extern "C" int fedbm_get_residual(fedbm_solver* s, double* r, int32_t on_device) {
-  int rc = check_solver(s);
-  if (rc) return rc;
-  if (!r) return fail(FEDBM_EINVAL, "null output");
-  double* dst = r;
-  if (!on_device) {
-    if ((rc = ensure_staging(s))) return rc;
-    dst = s->staging;
-  }
-  const int64_t n = s->K * s->Np * s->Q;
-  const int g = grid_for(n, 256);
-  if (s->store == kStoreF64)
-    decode_residual_kernel<double><<<g, 256, 0, s->stream>>>(static_cast<const double*>(s->res), dst, s->K, s->Np, s->Q, s->Qp);
-  else
-    decode_residual_kernel<float><<<g, 256, 0, s->stream>>>(static_cast<const float*>(s->res), dst, s->K, s->Np, s->Q, s->Qp);
-  FEDBM_CK(cudaGetLastError());
-  if (!on_device) {
-    FEDBM_CK(cudaMemcpyAsync(r, dst, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-    FEDBM_CK(cudaStreamSynchronize(s->stream));
-  }
-  return FEDBM_OK;
-}
-
-// ---------------------------------------------------------------- stepping
 extern "C" int fedbm_rk_step(fedbm_solver* s, int32_t nsteps) {
-  int rc = check_solver(s);
-  if (rc) return rc;
-  if (nsteps < 0) return fail(FEDBM_EINVAL, "nsteps must be >= 0");
-  if ((rc = build_graphs(s))) return rc;
-  for (int n = 0; n < nsteps; ++n) {
-    FEDBM_CK(cudaGraphLaunch(s->graph[s->cur], s->stream));
-    s->cur = 1 - s->cur;  // five stages: the state ends in the other buffer
-    s->time += s->dt;
-    s->steps += 1;
-  }
-  return FEDBM_OK;
+  FEDBM_SOLVER(s);
+  return rk_step(B, nsteps);
 }
 
 extern "C" int fedbm_rk_stage(fedbm_solver* s, int32_t stage) {
-  int rc = check_solver(s);
-  if (rc) return rc;
+  FEDBM_SOLVER(s);
   if (stage < 0 || stage > 4) return fail(FEDBM_EINVAL, "stage must be in 0..4");
-  FEDBM_CK(launch_stage(s, stage, s->cur, s->stream));
-  s->cur = 1 - s->cur;
+  FEDBM_CK(launch_stage(B.groups[0], stage, B.cur, B.stream));
+  B.cur = 1 - B.cur;
   return FEDBM_OK;
 }
 
-// ---------------------------------------------------------------- diagnostics
 extern "C" int fedbm_get_moments(fedbm_solver* s, double* rho, double* ux, double* uy, int32_t on_device) {
-  int rc = check_solver(s);
-  if (rc) return rc;
-  const int64_t nodes = s->K * s->Np;
-  double *dr = rho, *dx = ux, *dy = uy;
-  if (!on_device) {
-    if (!s->mom) FEDBM_CK(cudaMalloc(&s->mom, size_t(3) * nodes * sizeof(double)));
-    dr = s->mom;
-    dx = s->mom + nodes;
-    dy = s->mom + 2 * nodes;
-  } else if (!rho || !ux || !uy) {
-    return fail(FEDBM_EINVAL, "device moments need three output pointers");
-  }
-  const int g = grid_for(nodes, 256);
-  switch (s->store) {
-    case kStoreF64: moments_kernel<StoreF64><<<g, 256, 0, s->stream>>>(s->f[s->cur], nullptr, s->vel64, s->K, s->Np, s->Qp, dr, dx, dy); break;
-    case kStoreF32: moments_kernel<StoreF32><<<g, 256, 0, s->stream>>>(s->f[s->cur], nullptr, s->vel64, s->K, s->Np, s->Qp, dr, dx, dy); break;
-    case kStoreBF16: moments_kernel<StoreBF16><<<g, 256, 0, s->stream>>>(s->f[s->cur], s->scale[s->cur], s->vel64, s->K, s->Np, s->Qp, dr, dx, dy); break;
-    default: moments_kernel<StoreF16><<<g, 256, 0, s->stream>>>(s->f[s->cur], s->scale[s->cur], s->vel64, s->K, s->Np, s->Qp, dr, dx, dy); break;
-  }
-  FEDBM_CK(cudaGetLastError());
-  if (!on_device) {
-    const size_t b = size_t(nodes) * sizeof(double);
-    if (rho) FEDBM_CK(cudaMemcpyAsync(rho, dr, b, cudaMemcpyDeviceToHost, s->stream));
-    if (ux) FEDBM_CK(cudaMemcpyAsync(ux, dx, b, cudaMemcpyDeviceToHost, s->stream));
-    if (uy) FEDBM_CK(cudaMemcpyAsync(uy, dy, b, cudaMemcpyDeviceToHost, s->stream));
-    FEDBM_CK(cudaStreamSynchronize(s->stream));
-  }
-  return FEDBM_OK;
+  FEDBM_SOLVER(s);
+  return get_moments(B, 0, rho, ux, uy, on_device);
+}
+
+extern "C" int fedbm_get_state(fedbm_solver* s, double* f, int32_t on_device) {
+  FEDBM_SOLVER(s);
+  return get_state(B, 0, f, on_device);
+}
+
+extern "C" int fedbm_get_residual(fedbm_solver* s, double* r, int32_t on_device) {
+  FEDBM_SOLVER(s);
+  return get_residual(B, 0, r, on_device);
 }
 
 extern "C" int fedbm_mass(fedbm_solver* s, double* total) {
-  int rc = check_solver(s);
+  FEDBM_SOLVER(s);
+  return mass(B, 0, total);
+}
+
+extern "C" int fedbm_info(const fedbm_solver* s, fedbm_info_t* out) {
+  if (!s || !s->b) return fail(FEDBM_EINVAL, "null solver");
+  return info(*s->b, 0, out);
+}
+
+// ---------------------------------------------------------------- batch
+extern "C" int fedbm_batch_create(const fedbm_case_desc* cases, int32_t ncases, void* cuda_stream,
+                                  fedbm_batch** out) {
+  if (!out) return fail(FEDBM_EINVAL, "null output");
+  *out = nullptr;
+  Batch* b = nullptr;
+  int rc = create_batch(cases, ncases, cuda_stream, &b);
   if (rc) return rc;
-  if (!total) return fail(FEDBM_EINVAL, "null output");
-  FEDBM_CK(cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream));
-  const int64_t nodes = s->K * s->Np;
-  const int g = int(std::min<int64_t>(kMassBlocks, (nodes + kMassThreads - 1) / kMassThreads));
-  switch (s->store) {
-    case kStoreF64: mass_partial_kernel<StoreF64><<<g, kMassThreads, 0, s->stream>>>(s->f[s->cur], nullptr, s->vel64, s->Jk, s->mw, s->K, s->Np, s->Qp, s->partial, s->flag); break;
-    case kStoreF32: mass_partial_kernel<StoreF32><<<g, kMassThreads, 0, s->stream>>>(s->f[s->cur], nullptr, s->vel64, s->Jk, s->mw, s->K, s->Np, s->Qp, s->partial, s->flag); break;
-    case kStoreBF16: mass_partial_kernel<StoreBF16><<<g, kMassThreads, 0, s->stream>>>(s->f[s->cur], s->scale[s->cur], s->vel64, s->Jk, s->mw, s->K, s->Np, s->Qp, s->partial, s->flag); break;
-    default: mass_partial_kernel<StoreF16><<<g, kMassThreads, 0, s->stream>>>(s->f[s->cur], s->scale[s->cur], s->vel64, s->Jk, s->mw, s->K, s->Np, s->Qp, s->partial, s->flag); break;
-  }
-  FEDBM_CK(cudaGetLastError());
-  mass_final_kernel<<<1, 256, 0, s->stream>>>(s->partial, g, s->partial + kMassBlocks);
-  FEDBM_CK(cudaGetLastError());
-  int flag[2] = {0, 0};
-  FEDBM_CK(cudaMemcpyAsync(total, s->partial + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  FEDBM_CK(cudaMemcpyAsync(flag, s->flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-  FEDBM_CK(cudaStreamSynchronize(s->stream));
-  if (flag[1]) return fail(FEDBM_ETIMEOUT, "a stage kernel's bounded wait for its tile copies gave up");
-  if (flag[0]) return fail(FEDBM_ENONFINITE, "state has a non-finite value or a node with rho <= 0");
+  fedbm_batch* h = new fedbm_batch();
+  h->b = b;
+  *out = h;
   return FEDBM_OK;
 }
 
-extern "C" int fedbm_info(const fedbm_solver* s, fedbm_info_t* info) {
-  if (!s || !info) return fail(FEDBM_EINVAL, "null argument");
-  info->K = s->K;
-  info->Np = s->Np;
-  info->Nfp = s->Nfp;
-  info->Q = s->Q;
-  info->Q_padded = s->Qp;
-  info->dt = s->dt;
-  info->tau = s->tau;
-  info->time = s->time;
-  info->steps = s->steps;
-  info->precision = s->prm.precision;
-  info->reduction = s->prm.reduction;
-  info->order = s->ops.p;
-  info->eq_order = s->vs_desc.eq_order;
-  info->elems_per_cta = s->epc;
-  info->threads_per_cta = s->tpb;
-  info->state_bytes = int64_t(s->K) * s->Np * s->Qp * int64_t(store_bytes(s->store));
-  info->residual_bytes = int64_t(s->K) * s->Np * s->Qp * int64_t(real_bytes(s->store));
-  return FEDBM_OK;
+extern "C" void fedbm_batch_destroy(fedbm_batch* h) {
+  if (!h) return;
+  free_batch(h->b);
+  delete h;
+}
+
+#define FEDBM_BATCH(h, c)                                       \
+  if (!(h)) return fail(FEDBM_EINVAL, "null batch");             \
+  Batch& B = *(h)->b;                                           \
+  do {                                                          \
+    int rc_ = check_batch(&B, (c));                             \
+    if (rc_) return rc_;                                        \
+  } while (0)
+
+extern "C" int fedbm_batch_set_state(fedbm_batch* h, int32_t c, const double* f, int32_t on_device) {
+  FEDBM_BATCH(h, c);
+  return set_state(B, c, f, on_device);
+}
+
+extern "C" int fedbm_batch_set_equilibrium(fedbm_batch* h, int32_t c, double rho0, double ux0, double uy0,
+                                           double amp, uint64_t seed) {
+  FEDBM_BATCH(h, c);
+  return set_equilibrium(B, c, rho0, ux0, uy0, amp, seed);
+}
+
+extern "C" int fedbm_batch_rk_step(fedbm_batch* h, int32_t nsteps) {
+  FEDBM_BATCH(h, 0);
+  return rk_step(B, nsteps);
+}
+
+extern "C" int fedbm_batch_get_state(fedbm_batch* h, int32_t c, double* f, int32_t on_device) {
+  FEDBM_BATCH(h, c);
+  return get_state(B, c, f, on_device);
+}
+
+extern "C" int fedbm_batch_get_moments(fedbm_batch* h, int32_t c, double* rho, double* ux, double* uy,
+                                       int32_t on_device) {
+  FEDBM_BATCH(h, c);
+  return get_moments(B, c, rho, ux, uy, on_device);
+}
+
+extern "C" int fedbm_batch_mass(fedbm_batch* h, int32_t c, double* total) {
+  FEDBM_BATCH(h, c);
+  return mass(B, c, total);
+}
+
+extern "C" int fedbm_batch_info(const fedbm_batch* h, int32_t c, fedbm_info_t* out) {
+  if (!h || !h->b) return fail(FEDBM_EINVAL, "null batch");
+  if (c < 0 || c >= int(h->b->cases.size())) return fail(FEDBM_EINVAL, "case index out of range");
+  return info(*h->b, c, out);
+}
+
+extern "C" int fedbm_batch_set_tiles(fedbm_batch* h, int32_t group, int32_t elems_per_cta, int32_t threads_per_cta,
+                                     int32_t pipeline_stages) {
+  FEDBM_BATCH(h, 0);
+  if (group < 0 || group >= int(B.groups.size())) return fail(FEDBM_EINVAL, "group index out of range");
+  return configure_tiles(B, B.groups[group], elems_per_cta, threads_per_cta, pipeline_stages);
 }

@@ -49,7 +49,11 @@ enum VelRow { kVelEx = 0, kVelEy = 1, kVelW = 2, kVelInvW = 3, kVelWex = 4, kVel
 // Reduction modes for the velocity moments (enum fedbm_reduction).
 enum RedMode { kRedDefault = 0, kRedFP64 = 1, kRedCompFP32 = 2 };
 
+// Per-element record [kGeoStrideDev]: r_x, s_x, r_y, s_y, then (n_x, n_y, Fscale)
+// for faces 0..2, the Jacobian J, the time step and 1/tau of the element's case
+// (1/tau = 0 switches the collision term off).
 constexpr int kGeoStrideDev = 16;
+constexpr int kGeoJ = 13, kGeoDt = 14, kGeoInvTau = 15;
 
 // Kernel arguments (by value).  Pointers are device pointers of the solver.
 template <typename R>
@@ -62,14 +66,15 @@ struct StageArgs {
   const int32_t* nbr;       // [K][3] face codes
   const R* geo;             // [K][16] geometry
   const R* vel;             // [kVelRows][Qp]
-  const R* wall_feq;        // [4][Qp] f^eq(1, u_b) per side
-  const R* wall_den_inv;    // [4] 1 / sum_{e.n<0} |e.n| f^eq(1,u_b) per side
-  int32_t wall_diffuse_mask;  // bit s set: side s is an eq. FullBC wall
+  const R* wall_feq;        // [slots][Qp] f^eq(1, u_b) per wall slot (4 * case + side)
+  const R* wall_den_inv;    // [slots] 1 / sum_{e.n<0} |e.n| f^eq(1,u_b); 0 for eq. UsedBC walls
+  int32_t wall_any;         // 1 if some slot is an eq. FullBC wall
   R W0, W1x, W1y;           // sum w, sum w ex, sum w ey (deviation moments)
   int64_t K;
   int32_t Qp;
-  int32_t epc;              // elements per CTA
-  R dt, rkA, rkB, inv_tau, ab;
+  int32_t epc;              // elements per CTA tile
+  int32_t nstages;          // 2: double-buffered tile pipeline, 1: single buffer
+  R rkA, rkB, ab;
   int32_t collision, eq_order, red;
   int* err;                 // set to 1 if a bounded wait of a CTA gave up
 };
@@ -94,7 +99,7 @@ __host__ __device__ inline size_t stage_smem_layout(int Np, int NF, int epc, int
   off[kSmScale] = b;  b += align16(size_t(epc) * 4);                  // element scale (deviation forms)
   off[kSmNScale] = b; b += align16(size_t(epc) * 3 * 4);              // neighbour scales, then new scale
   off[kSmDmax] = b;   b += align16(size_t(epc) * 4);
-  off[kSmMom] = b;    b += align16(size_t(epc) * Np * 4 * r_bytes);   // rho, ux, uy per node
+  off[kSmMom] = b;    b += align16(size_t(epc) * Np * 8 * r_bytes);   // f^eq/tau coefficients per node
   off[kSmWn] = b;     b += align16(size_t(epc) * NF * r_bytes);        // wall numerators
   off[kSmEnd] = b;
   return b;
@@ -134,11 +139,17 @@ __device__ inline StageSmem<R, S> carve_stage_smem(unsigned char* base, int Np, 
   return s;
 }
 
-__host__ inline size_t stage_smem_bytes(int p, int store_kind, int epc, int Qp) {
+// Bytes between the two pipeline stages of a CTA (one stage, 128-byte aligned).
+__host__ __device__ inline size_t stage_smem_stride(int Np, int NF, int epc, int Qp, size_t s_bytes, size_t r_bytes) {
+  size_t off[kSmEnd + 1];
+  return (stage_smem_layout(Np, NF, epc, Qp, s_bytes, r_bytes, off) + 127) & ~size_t(127);
+}
+
+// Dynamic shared memory of one stage CTA with `nstages` pipeline stages.
+__host__ inline size_t stage_smem_bytes(int p, int store_kind, int epc, int Qp, int nstages) {
   const size_t s_bytes = store_kind == kStoreF64 ? 8 : store_kind == kStoreF32 ? 4 : 2;
   const size_t r_bytes = store_kind == kStoreF64 ? 8 : 4;
-  size_t off[kSmEnd + 1];
-  return stage_smem_layout(np_of(p), 3 * (p + 1), epc, Qp, s_bytes, r_bytes, off);
+  return size_t(nstages) * stage_smem_stride(np_of(p), 3 * (p + 1), epc, Qp, s_bytes, r_bytes);
 }
 
 }  // namespace fedbm

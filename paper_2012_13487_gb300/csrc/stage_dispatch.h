@@ -8,8 +8,9 @@ namespace fedbm {
 
 struct StageEntry {
   cudaError_t (*launch)(int store_kind, const void* args, int grid, int block, size_t smem, cudaStream_t st);
-  cudaError_t (*set_smem)(int store_kind, size_t smem);
+  cudaError_t (*set_smem)(int store_kind, int Qp, size_t smem);
   cudaError_t (*upload)(const double* Dr, const double* Ds, const double* LIFT);
+  int (*occupancy)(int store_kind, int Qp, int block, size_t smem);  // resident CTAs per SM
 };
 
 StageEntry stage_entry_p0();

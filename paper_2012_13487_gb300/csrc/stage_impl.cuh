@@ -10,17 +10,18 @@
 // or eq. UsedBC (Sec. II.A.4).  It then applies the 2N-storage update
 //   res <- A res + dt rhs ; f <- f + B res
 // and writes the new state to the other state buffer (neighbours still read
-// the old one).  The reference operators Dr, Ds, LIFT live in constant memory
-// and every loop over nodes is unrolled, so they are immediate operands of
-// the FMAs.
+// the old one).
 //
 // Phases of a CTA:
-//   1. copy the element tile f[k0:k0+epc][Np][Qp] to shared memory (16-byte
-//      vectors), plus geometry, face codes and (deviation forms) scales;
-//   2. node moments rho, u (Sec. II.A.2) by a G-lane reduction per node;
+//   1. bulk-copy (TMA) the element tile f[k0:k0+epc][Np][Qp], the residual
+//      tile and every neighbour face row into shared memory;
+//   2. node moments rho, u (Sec. II.A.2) by a G-lane reduction per node, kept
+//      as the coefficients of f^eq/tau per node;
 //   3. wall numerators sum_{e.n>0} (e.n) f^- of eq. FullBC per wall node;
-//   4. per (element, velocity) item: residual, update and store;
-//   5. deviation forms only: per-element scale from max |f/w - 1|, encode.
+//   4. residual and update, one thread per (element, velocity) item, with
+//      Dr, Ds, LIFT as constant-memory operands of unrolled FMAs;
+//   5. deviation forms only: per-element scale from max |f/w - 1|, encode;
+//   6. bulk-store the new state and residual tiles.
 #include "device_common.cuh"
 #include "stage_dispatch.h"
 
@@ -156,10 +157,9 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src_smem, uint
                "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void bulk_commit_and_wait_read() {
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until every committed bulk store of this thread has finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -175,13 +175,13 @@ struct Vec16 {
 
 // Phase 2: rho, u_x, u_y of every node of the tile into s_mom.  G lanes share a
 // node; each lane reduces 16-byte chunks of the node's velocity row.
-template <class ST, class Acc>
+template <class ST, class Acc, int QT>
 __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename ST::S* s_f,
-                             const float* s_scale, typename ST::R* s_mom, int ne) {
+                             const float* s_scale, const typename ST::R* s_geo, typename ST::R* s_mom, int ne) {
   using R = typename ST::R;
   using S = typename ST::S;
   constexpr int V = Vec16<ST>::N;
-  const int Qp = a.Qp, tid = threadIdx.x, nth = blockDim.x;
+  const int Qp = QT > 0 ? QT : a.Qp, tid = threadIdx.x, nth = blockDim.x;
   const int nchunk = Qp / V;
   int G = pow2_floor_32(nth / (a.epc * NP));
   while (G > 1 && G > nchunk) G >>= 1;
@@ -198,54 +198,74 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
       const S* row = s_f + size_t(pair) * Qp;
       for (int c = lane; c < nchunk; c += G) {
         __align__(16) S v[V];
+        __align__(16) R exv[V], eyv[V], wvv[V];
         *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(row + c * V);
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-          const int i = c * V + j;
-          if constexpr (ST::dev) {
-            const float wq = __ldg(wv + i) * ST::to_r(v[j]);
-            m0.add(wq);
-            m1.add(__ldg(ex + i) * wq);
-            m2.add(__ldg(ey + i) * wq);
-          } else {
-            const R f = v[j];
-            m0.add(f);
-            m1.add(__ldg(ex + i) * f);
-            m2.add(__ldg(ey + i) * f);
-          }
+        for (int j = 0; j < V * int(sizeof(R)) / 16; ++j) {
+          reinterpret_cast<uint4*>(exv)[j] = __ldg(reinterpret_cast<const uint4*>(ex + c * V) + j);
+          reinterpret_cast<uint4*>(eyv)[j] = __ldg(reinterpret_cast<const uint4*>(ey + c * V) + j);
+          if constexpr (ST::dev) reinterpret_cast<uint4*>(wvv)[j] = __ldg(reinterpret_cast<const uint4*>(wv + c * V) + j);
         }
+        // sums over the chunk in the compute precision, then one accumulator
+        // update per chunk (FP64 or compensated across chunks)
+        R c0 = 0, c1 = 0, c2 = 0;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+          R f;
+          if constexpr (ST::dev) f = wvv[j] * ST::to_r(v[j]);
+          else f = v[j];
+          c0 += f;
+          c1 = fma(exv[j], f, c1);
+          c2 = fma(eyv[j], f, c2);
+        }
+        m0.add(c0);
+        m1.add(c1);
+        m2.add(c2);
       }
     }
     m0.reduce(G);
     m1.reduce(G);
     m2.reduce(G);
     if (valid && lane == 0) {
-      double rho, jx, jy;
+      // in the compute precision R: FP64 arithmetic is kept out of the FP32 paths
+      R rho, jx, jy;
       if constexpr (ST::dev) {
-        const double sc = s_scale[pair / NP];
-        rho = double(a.W0) + sc * double(m0.value());
-        jx = double(a.W1x) + sc * double(m1.value());
-        jy = double(a.W1y) + sc * double(m2.value());
+        const R sc = s_scale[pair / NP];
+        rho = a.W0 + sc * R(m0.value());
+        jx = a.W1x + sc * R(m1.value());
+        jy = a.W1y + sc * R(m2.value());
       } else {
-        rho = m0.value();
-        jx = m1.value();
-        jy = m2.value();
+        rho = R(m0.value());
+        jx = R(m1.value());
+        jy = R(m2.value());
       }
-      R* mm = s_mom + size_t(pair) * 4;
-      mm[0] = R(rho);
-      mm[1] = R(jx / rho);
-      mm[2] = R(jy / rho);
+      // f^eq_i / tau = w_i [m0 + e_x m1 + e_y m2 + m3 (e.u)^2 + (e.u)(m6 (e.u)^2 - m7)]
+      // with e.u = e_x m4 + e_y m5 (eq. feq; the m6, m7 terms are the third
+      // Hermite order of eq. Herm3a and vanish for eq_order 2)
+      const R irho = R(1) / rho;
+      const R it = s_geo[(pair / NP) * kGeoStrideDev + kGeoInvTau];  // 1/tau of the element's case
+      const R ux = jx * irho, uy = jy * irho, uu = ux * ux + uy * uy;
+      const bool third = a.eq_order == 3;
+      R* mm = s_mom + size_t(pair) * 8;
+      mm[0] = rho * (R(1) - R(0.5) * uu) * it;
+      mm[1] = jx * it;
+      mm[2] = jy * it;
+      mm[3] = R(0.5) * rho * it;
+      mm[4] = ux;
+      mm[5] = uy;
+      mm[6] = third ? rho * it * R(1.0 / 6.0) : R(0);
+      mm[7] = third ? R(0.5) * rho * uu * it : R(0);
     }
   }
 }
 
 // Phase 3: numerators of eq. FullBC, sum over outgoing velocities of (e.n) f^-.
-template <class ST>
+template <class ST, int QT>
 __device__ void tile_wall_numerators(const StageArgs<typename ST::R>& a, const typename ST::S* s_f,
                                      const typename ST::R* s_geo, const int* s_nbr,
                                      const float* s_scale, typename ST::R* s_wn, int ne) {
   using R = typename ST::R;
-  const int Qp = a.Qp, tid = threadIdx.x, nth = blockDim.x;
+  const int Qp = QT > 0 ? QT : a.Qp, tid = threadIdx.x, nth = blockDim.x;
   const int G = pow2_floor_32(nth / (a.epc * NF));
   const int ngroups = nth / G, grp = tid / G, lane = tid % G;
   const int ntrip = ne * NF;
@@ -258,7 +278,7 @@ __device__ void tile_wall_numerators(const StageArgs<typename ST::R>& a, const t
     bool active = false;
     if (trip < ntrip) {
       const int code = s_nbr[e * 3 + fc];
-      active = code < 0 && ((a.wall_diffuse_mask >> (-code - 1)) & 1);
+      active = code < 0 && __ldg(a.wall_den_inv + (-code - 1)) > R(0);
     }
     R acc = 0;
     if (active) {
@@ -286,265 +306,374 @@ __device__ __forceinline__ typename ST::R new_f(typename ST::R fold, typename ST
   return fma(rkB, r, fold);
 }
 
+// tau-scaled collision term w f^eq(rho, u)/tau - f/tau of one value, from the
+// node record written by tile_moments (all zero when collision is off)
+template <typename R>
+__device__ __forceinline__ R collision(const R* mm, R ex, R ey, R w, R f, R inv_tau, bool third) {
+  const R eu = ex * mm[4] + ey * mm[5];
+  R feq = fma(ey, mm[2], fma(ex, mm[1], mm[0]));
+  feq = fma(eu, mm[3] * eu, feq);
+  if (third) feq = fma(eu, fma(mm[6], eu * eu, -mm[7]), feq);
+  return fma(w, feq, -inv_tau * f);
+}
+
 // Minimum resident CTAs of 256 threads per SM: bounds the registers per thread
 // (65536 / (256 * min)) so that the unrolled node loop does not spill.
 template <class ST>
-constexpr int stage_min_blocks() {
+__host__ __device__ constexpr int stage_min_blocks() {
   return sizeof(typename ST::R) == 8 ? 2 : (P <= 3 ? 4 : (P <= 5 ? 3 : 2));
 }
 
-template <class ST>
+
+// Bulk copies (TMA) of one tile into a shared-memory stage, issued by warp 0:
+// element tile, residual tile (stages 2..5), geometry and every neighbour face
+// row, all completing on the stage's mbarrier; the lanes also store the face
+// codes (and for the deviation forms the scales) of the tile.
+template <class ST, int QT>
+__device__ void issue_tile_loads(const StageArgs<typename ST::R>& a, StageSmem<typename ST::R, typename ST::S>& sm,
+                                 int64_t k0, int ne, bool read_res) {
+  using R = typename ST::R;
+  using S = typename ST::S;
+  const int lane = threadIdx.x & 31;
+  const int Qp = QT > 0 ? QT : a.Qp;
+  const size_t row_bytes = size_t(Qp) * sizeof(S);
+  const S* fin = static_cast<const S*>(a.f_in);
+  const uint32_t tile_bytes = uint32_t(size_t(ne) * NP * row_bytes);
+  const uint32_t res_bytes = uint32_t(size_t(ne) * NP * Qp * sizeof(R));
+  const uint32_t geo_bytes = uint32_t(size_t(ne) * kGeoStrideDev * sizeof(R));
+  // plain shared-memory stores first: the release of the arrive below makes
+  // them visible to every thread that waits on the barrier
+  for (int v = lane; v < ne * 3; v += 32) {
+    const int code = __ldg(a.nbr + k0 * 3 + v);
+    sm.nbr[v] = code;
+    if constexpr (ST::dev) sm.nscale[v] = code >= 0 ? __ldg(a.scale_in + (code >> 3)) : 0.f;
+  }
+  if constexpr (ST::dev) {
+    for (int v = lane; v < ne; v += 32) {
+      sm.scale[v] = __ldg(a.scale_in + k0 + v);
+      sm.dmax[v] = 0u;
+    }
+  }
+  uint32_t bytes = 0;
+  if (lane == 0) bytes += tile_bytes + geo_bytes + (read_res ? res_bytes : 0u);
+  for (int row = lane; row < ne * NF; row += 32) {
+    const int code = __ldg(a.nbr + (k0 + row / NF) * 3 + (row % NF) / NFP);
+    if (code >= 0) bytes += uint32_t(row_bytes);
+  }
+  mbar_arrive_expect_tx(sm.bar, bytes);
+  if (lane == 0) {
+    bulk_load(sm.f, fin + k0 * NP * Qp, tile_bytes, sm.bar);
+    bulk_load(sm.geo, a.geo + k0 * kGeoStrideDev, geo_bytes, sm.bar);
+    if (read_res) bulk_load(sm.res, a.res + k0 * NP * Qp, res_bytes, sm.bar);
+  }
+  for (int row = lane; row < ne * NF; row += 32) {
+    const int e = row / NF, fc = (row % NF) / NFP, aa = row % NFP;
+    const int code = __ldg(a.nbr + (k0 + e) * 3 + fc);
+    if (code >= 0) {
+      const int64_t kn = code >> 3;
+      const int fn = (code >> 1) & 3;
+      const int a2 = (code & 1) ? NFP - 1 - aa : aa;
+      const int rs = a2 * (P + 1) - a2 * (a2 - 1) / 2;
+      const int node = fn == 0 ? a2 : (fn == 1 ? rs + (P - a2) : rs);
+      bulk_load(sm.tr + size_t(row) * Qp, fin + (kn * NP + node) * Qp, uint32_t(row_bytes), sm.bar);
+    }
+  }
+}
+
+// Persistent kernel: CTA b handles tiles b, b + gridDim.x, ... through two
+// shared-memory stages, loading tile j+1 while it computes tile j.
+// QT > 0: the padded velocity count is the compile-time constant QT (all
+// shared-memory strides become immediate offsets); QT = 0: taken from a.Qp.
+template <class ST, int QT>
 __global__ void __launch_bounds__(256, stage_min_blocks<ST>()) stage_kernel(const StageArgs<typename ST::R> a) {
   using R = typename ST::R;
   using S = typename ST::S;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int epc = a.epc, Qp = a.Qp;
-  const int64_t k0 = int64_t(blockIdx.x) * epc;
-  const int ne = int(min(int64_t(epc), a.K - k0));
+  const int epc = a.epc, Qp = QT > 0 ? QT : a.Qp;
   const int tid = threadIdx.x, nth = blockDim.x;
   const R rkA = a.rkA;
   const bool read_res = rkA != R(0);
-
-  StageSmem<R, S> sm = carve_stage_smem<R, S>(smem, NP, NF, epc, Qp);
-  const S* fin = static_cast<const S*>(a.f_in);
+  const int64_t ntiles = (a.K + epc - 1) / epc;
+  const size_t stage_bytes = stage_smem_stride(NP, NF, epc, Qp, sizeof(S), sizeof(R));
+  auto stage = [&](int sidx) { return carve_stage_smem<R, S>(smem + sidx * stage_bytes, NP, NF, epc, Qp); };
   const size_t row_bytes = size_t(Qp) * sizeof(S);
 
+  const bool two = a.nstages == 2;
   if (tid == 0) {
-    mbar_init(sm.bar, 32);
+    mbar_init(stage(0).bar, 32);
+    if (two) mbar_init(stage(1).bar, 32);  // the second stage exists only when nstages == 2
     fence_mbar_init();
     fence_proxy_async_smem();
   }
   __syncthreads();
 
-  // ---- 1. asynchronous tile load: element tile, residual tile, face traces ----
-  if (tid < 32) {
-    uint32_t bytes = 0;
-    const uint32_t tile_bytes = uint32_t(size_t(ne) * NP * row_bytes);
-    if (tid == 0) bytes += tile_bytes + (read_res ? uint32_t(size_t(ne) * NP * Qp * sizeof(R)) : 0u);
-    for (int row = tid; row < ne * NF; row += 32) {
-      const int code = __ldg(a.nbr + (k0 + row / NF) * 3 + (row % NF) / NFP);
-      if (code >= 0) bytes += uint32_t(row_bytes);
-    }
-    mbar_arrive_expect_tx(sm.bar, bytes);
-    if (tid == 0) {
-      bulk_load(sm.f, fin + k0 * NP * Qp, tile_bytes, sm.bar);
-      if (read_res) bulk_load(sm.res, a.res + k0 * NP * Qp, uint32_t(size_t(ne) * NP * Qp * sizeof(R)), sm.bar);
-    }
-    for (int row = tid; row < ne * NF; row += 32) {
-      const int e = row / NF, fc = (row % NF) / NFP, aa = row % NFP;
-      const int code = __ldg(a.nbr + (k0 + e) * 3 + fc);
-      if (code >= 0) {
-        const int64_t kn = code >> 3;
-        const int fn = (code >> 1) & 3;
-        const int a2 = (code & 1) ? NFP - 1 - aa : aa;
-        const int rs = a2 * (P + 1) - a2 * (a2 - 1) / 2;
-        const int node = fn == 0 ? a2 : (fn == 1 ? rs + (P - a2) : rs);
-        bulk_load(sm.tr + size_t(row) * Qp, fin + (kn * NP + node) * Qp, uint32_t(row_bytes), sm.bar);
-      }
-    }
-  }
-  for (int v = tid; v < ne * kGeoStrideDev; v += nth) sm.geo[v] = a.geo[k0 * kGeoStrideDev + v];
-  for (int v = tid; v < ne * 3; v += nth) {
-    const int code = a.nbr[k0 * 3 + v];
-    sm.nbr[v] = code;
-    if constexpr (ST::dev) sm.nscale[v] = code >= 0 ? a.scale_in[code >> 3] : 0.f;
-  }
-  if constexpr (ST::dev) {
-    for (int v = tid; v < ne; v += nth) {
-      sm.scale[v] = a.scale_in[k0 + v];
-      sm.dmax[v] = 0u;
-    }
-  }
-  __syncthreads();
-  if (!mbar_wait_bounded(sm.bar, 0, 2000000000ull)) {
-    if (a.err) atomicExch(a.err, 1);
-    mbar_wait_bounded(sm.bar, 0, 1000000000ull);  // let copies in flight land before exit
-    return;
+  int64_t tile = blockIdx.x;
+  if (tid < 32 && tile < ntiles) {
+    StageSmem<R, S> s0 = stage(0);
+    issue_tile_loads<ST, QT>(a, s0, tile * epc, int(min(int64_t(epc), a.K - tile * epc)), read_res);
   }
 
-  // ---- 2. node moments ---------------------------------------------------------
-  if (a.collision) {
-    if constexpr (sizeof(R) == 8) {
-      tile_moments<ST, AccD>(a, sm.f, sm.scale, sm.mom, ne);
+  for (int j = 0; tile < ntiles; ++j, tile += gridDim.x) {
+    StageSmem<R, S> sm = stage(two ? (j & 1) : 0);
+    const uint32_t parity = uint32_t((two ? (j >> 1) : j) & 1);
+    const int64_t k0 = tile * epc;
+    const int ne = int(min(int64_t(epc), a.K - k0));
+    const int64_t next = tile + gridDim.x;
+    if (tid < 32) {
+      if (two && next < ntiles) {
+        // prefetch the next tile into the other stage once its bulk store has read it
+        if (tid == 0) bulk_wait_read();
+        __syncwarp();
+        StageSmem<R, S> sn = stage((j + 1) & 1);
+        issue_tile_loads<ST, QT>(a, sn, next * epc, int(min(int64_t(epc), a.K - next * epc)), read_res);
+      } else if (!two && j > 0) {
+        // single stage: load this tile once the previous tile's store has read it
+        if (tid == 0) bulk_wait_read();
+        __syncwarp();
+        issue_tile_loads<ST, QT>(a, sm, k0, ne, read_res);
+      }
+    }
+    if (!mbar_wait_bounded(sm.bar, parity, 2000000000ull)) {
+      if (a.err) atomicExch(a.err, 1);
+      // let copies still in flight land before the CTA exits
+      if (two && next < ntiles) mbar_wait_bounded(stage((j + 1) & 1).bar, uint32_t(((j + 1) >> 1) & 1), 1000000000ull);
+      if (tid == 0) bulk_wait_read();
+      return;
+    }
+
+    // ---- 2. node moments ---------------------------------------------------------
+    if (!a.collision) {
+      for (int v = tid; v < ne * NP * 8; v += nth) sm.mom[v] = R(0);
     } else {
-      if (a.red == kRedFP64) tile_moments<ST, AccD>(a, sm.f, sm.scale, sm.mom, ne);
-      else if (a.red == kRedCompFP32) tile_moments<ST, AccN>(a, sm.f, sm.scale, sm.mom, ne);
-      else tile_moments<ST, AccF>(a, sm.f, sm.scale, sm.mom, ne);
+      if constexpr (sizeof(R) == 8) {
+        tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne);
+      } else {
+        if (a.red == kRedFP64) tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne);
+        else if (a.red == kRedCompFP32) tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne);
+        else tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne);
+      }
     }
-  }
-  // ---- 3. wall numerators ------------------------------------------------------
-  if (a.wall_diffuse_mask) tile_wall_numerators<ST>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, ne);
-  __syncthreads();
+    // ---- 3. wall numerators ------------------------------------------------------
+    if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, ne);
+    __syncthreads();
 
-  // ---- 4. residual and update per (element, velocity) ---------------------------
-  const R dt = a.dt, rkB = a.rkB, ab = a.ab, inv_tau = a.inv_tau;
-  float dmax = 0.f;
-  int emax = -1;
-  for (int item = tid; item < ne * Qp; item += nth) {
-    const int e = item / Qp;
-    const int i = item - e * Qp;
-    const R ex = __ldg(a.vel + kVelEx * Qp + i), ey = __ldg(a.vel + kVelEy * Qp + i);
-    const R w = __ldg(a.vel + kVelW * Qp + i);
-    const R* g = sm.geo + e * kGeoStrideDev;
-    const R ar = ex * g[0] + ey * g[2];
-    const R as = ex * g[1] + ey * g[3];
-    R ws = 0;
-    if constexpr (ST::dev) ws = w * sm.scale[e];
-    S* frow = sm.f + size_t(e) * NP * Qp + i;
-    R* rrow = sm.res + size_t(e) * NP * Qp + i;
+    // ---- 4. residual and update ----------------------------------------------------
+    float dmax = 0.f;  // deviation forms: running max |f/w - 1| of element emax
+    int emax = -1;
+    {
+    const R rkB = a.rkB, ab = a.ab;
+    const bool third = a.eq_order == 3;
+    for (int item = tid; item < ne * Qp; item += nth) {
+      const int e = item / Qp;
+      const int i = item - e * Qp;
+      const R ex = __ldg(a.vel + kVelEx * Qp + i), ey = __ldg(a.vel + kVelEy * Qp + i);
+      const R w = __ldg(a.vel + kVelW * Qp + i);
+      const R* g = sm.geo + e * kGeoStrideDev;
+      const R ar = ex * g[0] + ey * g[2];
+      const R as = ex * g[1] + ey * g[3];
+      const R dt = g[kGeoDt], inv_tau = g[kGeoInvTau];  // per element: cases of a batch differ
+      R ws = 0;
+      if constexpr (ST::dev) ws = w * sm.scale[e];
+      S* frow = sm.f + size_t(e) * NP * Qp + i;
+      R* rrow = sm.res + size_t(e) * NP * Qp + i;
 
-    R fr[NP];
-#pragma unroll
-    for (int m = 0; m < NP; ++m) fr[m] = decode<ST>(frow[m * Qp], w, ws);
+      R fr[NP];
+  #pragma unroll
+      for (int m = 0; m < NP; ++m) fr[m] = decode<ST>(frow[m * Qp], w, ws);
 
-    R flux[NF];
-#pragma unroll
-    for (int fc = 0; fc < 3; ++fc) {
-      const R en = ex * g[4 + 3 * fc] + ey * g[5 + 3 * fc];
-      const R c = R(0.5) * (en - ab * fabs(en)) * g[6 + 3 * fc];
-      const int code = sm.nbr[e * 3 + fc];
-      if (code >= 0) {
-        R wsn = 0;
-        if constexpr (ST::dev) wsn = w * sm.nscale[e * 3 + fc];
-        const S* trow = sm.tr + size_t(e * NF + fc * NFP) * Qp + i;
-#pragma unroll
-        for (int aa = 0; aa < NFP; ++aa)
-          flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - decode<ST>(trow[aa * Qp], w, wsn));
-      } else if (en < R(0)) {
-        const int side = -code - 1;
-        const R fb = __ldg(a.wall_feq + side * Qp + i);
-        const bool diffuse = (a.wall_diffuse_mask >> side) & 1;
-        const R scale = diffuse ? __ldg(a.wall_den_inv + side) * fb : R(0);
-#pragma unroll
-        for (int aa = 0; aa < NFP; ++aa) {
-          const R fp = diffuse ? sm.wn[e * NF + fc * NFP + aa] * scale : fb;
-          flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - fp);
+      R flux[NF];
+  #pragma unroll
+      for (int fc = 0; fc < 3; ++fc) {
+        const R en = ex * g[4 + 3 * fc] + ey * g[5 + 3 * fc];
+        const R c = R(0.5) * (en - ab * fabs(en)) * g[6 + 3 * fc];
+        const int code = sm.nbr[e * 3 + fc];
+        if (code >= 0) {
+          R wsn = 0;
+          if constexpr (ST::dev) wsn = w * sm.nscale[e * 3 + fc];
+          const S* trow = sm.tr + size_t(e * NF + fc * NFP) * Qp + i;
+  #pragma unroll
+          for (int aa = 0; aa < NFP; ++aa)
+            flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - decode<ST>(trow[aa * Qp], w, wsn));
+        } else if (en < R(0)) {
+          const int slot = -code - 1;  // wall slot: 4 * case + side
+          const R fb = __ldg(a.wall_feq + slot * Qp + i);
+          const R den_inv = __ldg(a.wall_den_inv + slot);
+          const bool diffuse = den_inv > R(0);
+          const R scale = diffuse ? den_inv * fb : R(0);
+  #pragma unroll
+          for (int aa = 0; aa < NFP; ++aa) {
+            const R fp = diffuse ? sm.wn[e * NF + fc * NFP + aa] * scale : fb;
+            flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - fp);
+          }
+        } else {
+  #pragma unroll
+          for (int aa = 0; aa < NFP; ++aa) flux[fc * NFP + aa] = R(0);
         }
-      } else {
-#pragma unroll
-        for (int aa = 0; aa < NFP; ++aa) flux[fc * NFP + aa] = R(0);
       }
-    }
 
-    float dloc = 0.f;
-    R invw = 0;
-    if constexpr (ST::dev) invw = __ldg(a.vel + kVelInvW * Qp + i);
-#pragma unroll
-    for (int n = 0; n < NP; ++n) {
-      R dr = 0, ds = 0;
-#pragma unroll
-      for (int m = 0; m < NP; ++m) {
-        dr = fma(opv<R>(OFF_DR + n * NP + m), fr[m], dr);
-        ds = fma(opv<R>(OFF_DS + n * NP + m), fr[m], ds);
+      float dloc = 0.f;
+      R invw = 0;
+      if constexpr (ST::dev) invw = __ldg(a.vel + kVelInvW * Qp + i);
+  #pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        R dr = 0, ds = 0;
+  #pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          dr = fma(opv<R>(OFF_DR + n * NP + m), fr[m], dr);
+          ds = fma(opv<R>(OFF_DS + n * NP + m), fr[m], ds);
+        }
+        R lf = 0;
+  #pragma unroll
+        for (int j = 0; j < NF; ++j) lf = fma(opv<R>(OFF_LIFT + n * NF + j), flux[j], lf);
+        R rhs = fma(-ar, dr, fma(-as, ds, lf));
+        rhs += collision<R>(sm.mom + (size_t(e) * NP + n) * 8, ex, ey, w, fr[n], inv_tau, third);
+        R r = dt * rhs;
+        if (read_res) r = fma(rkA, rrow[n * Qp], r);
+        rrow[n * Qp] = r;
+        const R fnew = new_f<ST>(fr[n], rkB, r);
+        if constexpr (ST::dev) {
+          dloc = fmaxf(dloc, fabsf((fnew - w) * invw));
+        } else {
+          frow[n * Qp] = S(fnew);
+        }
       }
-      R lf = 0;
-#pragma unroll
-      for (int j = 0; j < NF; ++j) lf = fma(opv<R>(OFF_LIFT + n * NF + j), flux[j], lf);
-      R rhs = lf - (ar * dr + as * ds);
-      if (a.collision) {
-        const R* mm = sm.mom + (size_t(e) * NP + n) * 4;
-        const R rho = mm[0], ux = mm[1], uy = mm[2];
-        const R eu = ex * ux + ey * uy, uu = ux * ux + uy * uy;
-        R poly = R(1) + eu + R(0.5) * (eu * eu - uu);
-        if (a.eq_order == 3) poly += eu * (eu * eu * R(1.0 / 6.0) - R(0.5) * uu);
-        rhs -= (fr[n] - w * rho * poly) * inv_tau;
-      }
-      R r = dt * rhs;
-      if (read_res) r = fma(rkA, rrow[n * Qp], r);
-      rrow[n * Qp] = r;
-      const R fnew = new_f<ST>(fr[n], rkB, r);
       if constexpr (ST::dev) {
-        dloc = fmaxf(dloc, fabsf((fnew - w) * invw));
-      } else {
-        frow[n * Qp] = S(fnew);
+        if (e != emax) {
+          if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
+          emax = e;
+          dmax = 0.f;
+        }
+        dmax = fmaxf(dmax, dloc);
       }
     }
+
+    }
+
+    // ---- 5. deviation forms: new per-element scale, encoding in place ------------
     if constexpr (ST::dev) {
-      if (e != emax) {
-        if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
-        emax = e;
-        dmax = 0.f;
+      if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
+      __syncthreads();
+      for (int e = tid; e < ne; e += nth) {
+        const float md = __uint_as_float(sm.dmax[e]);
+        float sc = 1.0f;
+        if (md > 0.f) {
+          int ex2;
+          frexpf(md, &ex2);
+          sc = ldexpf(1.0f, ex2 - ST::qmax_log2);
+        }
+        sm.nscale[e] = sc;  // face scales are no longer needed
+        a.scale_out[k0 + e] = sc;
       }
-      dmax = fmaxf(dmax, dloc);
+      __syncthreads();
+      constexpr int V = Vec16<ST>::N;
+      const int nvec = ne * NP * Qp / V;
+      for (int v = tid; v < nvec; v += nth) {
+        const int idx = v * V;
+        const int e = idx / (NP * Qp);
+        const int i0 = idx % Qp;
+        const float sold = sm.scale[e];
+        const float inv_s = 1.0f / sm.nscale[e];
+        __align__(16) S q[V];
+        *reinterpret_cast<uint4*>(q) = *reinterpret_cast<const uint4*>(sm.f + idx);
+  #pragma unroll
+        for (int j = 0; j < V; ++j) {
+          const float w = __ldg(a.vel + kVelW * Qp + i0 + j);
+          const float invw = __ldg(a.vel + kVelInvW * Qp + i0 + j);
+          const float fold = decode<ST>(q[j], w, w * sold);
+          const float fnew = new_f<ST>(fold, a.rkB, sm.res[idx + j]);
+          q[j] = ST::from_r((fnew - w) * invw * inv_s);
+        }
+        *reinterpret_cast<uint4*>(sm.f + idx) = *reinterpret_cast<const uint4*>(q);
+      }
     }
-  }
 
-  // ---- 5. deviation forms: new per-element scale, encoding in place ------------
-  if constexpr (ST::dev) {
-    if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
-    __syncthreads();
-    for (int e = tid; e < ne; e += nth) {
-      const float md = __uint_as_float(sm.dmax[e]);
-      float sc = 1.0f;
-      if (md > 0.f) {
-        int ex2;
-        frexpf(md, &ex2);
-        sc = ldexpf(1.0f, ex2 - ST::qmax_log2);
-      }
-      sm.nscale[e] = sc;  // face scales are no longer needed
-      a.scale_out[k0 + e] = sc;
-    }
-    __syncthreads();
-    constexpr int V = Vec16<ST>::N;
-    const int nvec = ne * NP * Qp / V;
-    for (int v = tid; v < nvec; v += nth) {
-      const int idx = v * V;
-      const int e = idx / (NP * Qp);
-      const int i0 = idx % Qp;
-      const float sold = sm.scale[e];
-      const float inv_s = 1.0f / sm.nscale[e];
-      __align__(16) S q[V];
-      *reinterpret_cast<uint4*>(q) = *reinterpret_cast<const uint4*>(sm.f + idx);
-#pragma unroll
-      for (int j = 0; j < V; ++j) {
-        const float w = __ldg(a.vel + kVelW * Qp + i0 + j);
-        const float invw = __ldg(a.vel + kVelInvW * Qp + i0 + j);
-        const float fold = decode<ST>(q[j], w, w * sold);
-        const float fnew = new_f<ST>(fold, rkB, sm.res[idx + j]);
-        q[j] = ST::from_r((fnew - w) * invw * inv_s);
-      }
-      *reinterpret_cast<uint4*>(sm.f + idx) = *reinterpret_cast<const uint4*>(q);
-    }
-  }
 
-  // ---- 6. bulk store of the new state and residual tiles -------------------------
-  fence_proxy_async_smem();
-  __syncthreads();
-  if (tid == 0) {
-    bulk_store(static_cast<S*>(a.f_out) + k0 * NP * Qp, sm.f, uint32_t(size_t(ne) * NP * row_bytes));
-    bulk_store(a.res + k0 * NP * Qp, sm.res, uint32_t(size_t(ne) * NP * Qp * sizeof(R)));
-    bulk_commit_and_wait_read();
+    // ---- 6. bulk store of the new state and residual tiles -----------------------
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      bulk_store(static_cast<S*>(a.f_out) + k0 * NP * Qp, sm.f, uint32_t(size_t(ne) * NP * row_bytes));
+      bulk_store(a.res + k0 * NP * Qp, sm.res, uint32_t(size_t(ne) * NP * Qp * sizeof(R)));
+      bulk_commit();
+    }
   }
+  if (tid == 0) bulk_wait_read();
 }
 
-template <class ST>
+template <class ST, int QT>
 cudaError_t launch_one(const void* args, int grid, int block, size_t smem, cudaStream_t st) {
   const auto& a = *static_cast<const StageArgs<typename ST::R>*>(args);
-  stage_kernel<ST><<<grid, block, smem, st>>>(a);
+  stage_kernel<ST, QT><<<grid, block, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+// Velocity counts with a specialised kernel (the GH D2Q16 and NC 16x16 /
+// 32x32 sets); other counts use the runtime-stride kernel.
 template <class ST>
-cudaError_t set_smem_one(size_t smem) {
-  return cudaFuncSetAttribute(stage_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+cudaError_t launch_q(int Qp, const void* args, int grid, int block, size_t smem, cudaStream_t st) {
+  if constexpr (ST::kind != kStoreF64) {
+    if (Qp == 16) return launch_one<ST, 16>(args, grid, block, smem, st);
+    if (Qp == 256) return launch_one<ST, 256>(args, grid, block, smem, st);
+    if (Qp == 1024) return launch_one<ST, 1024>(args, grid, block, smem, st);
+  }
+  return launch_one<ST, 0>(args, grid, block, smem, st);
+}
+
+template <class ST>
+int occupancy_q(int Qp, int block, size_t smem) {
+  int n = 0;
+  auto occ = [&](auto kernel) { cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem); };
+  if constexpr (ST::kind != kStoreF64) {
+    if (Qp == 16) { occ(stage_kernel<ST, 16>); return n; }
+    if (Qp == 256) { occ(stage_kernel<ST, 256>); return n; }
+    if (Qp == 1024) { occ(stage_kernel<ST, 1024>); return n; }
+  }
+  occ(stage_kernel<ST, 0>);
+  return n;
+}
+
+// resident CTAs per SM of the kernel a launch with these parameters uses
+int occupancy(int store_kind, int Qp, int block, size_t smem) {
+  switch (store_kind) {
+    case kStoreF64: return occupancy_q<StoreF64>(Qp, block, smem);
+    case kStoreF32: return occupancy_q<StoreF32>(Qp, block, smem);
+    case kStoreBF16: return occupancy_q<StoreBF16>(Qp, block, smem);
+    case kStoreF16: return occupancy_q<StoreF16>(Qp, block, smem);
+  }
+  return 0;
+}
+
+template <class ST>
+cudaError_t set_smem_q(int Qp, size_t smem) {
+  auto set = [smem](auto kernel) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  };
+  if constexpr (ST::kind != kStoreF64) {
+    if (Qp == 16) return set(stage_kernel<ST, 16>);
+    if (Qp == 256) return set(stage_kernel<ST, 256>);
+    if (Qp == 1024) return set(stage_kernel<ST, 1024>);
+  }
+  return set(stage_kernel<ST, 0>);
 }
 
 cudaError_t launch(int store_kind, const void* args, int grid, int block, size_t smem, cudaStream_t st) {
+  const int Qp = store_kind == kStoreF64 ? static_cast<const StageArgs<double>*>(args)->Qp
+                                         : static_cast<const StageArgs<float>*>(args)->Qp;
   switch (store_kind) {
-    case kStoreF64: return launch_one<StoreF64>(args, grid, block, smem, st);
-    case kStoreF32: return launch_one<StoreF32>(args, grid, block, smem, st);
-    case kStoreBF16: return launch_one<StoreBF16>(args, grid, block, smem, st);
-    case kStoreF16: return launch_one<StoreF16>(args, grid, block, smem, st);
+    case kStoreF64: return launch_q<StoreF64>(Qp, args, grid, block, smem, st);
+    case kStoreF32: return launch_q<StoreF32>(Qp, args, grid, block, smem, st);
+    case kStoreBF16: return launch_q<StoreBF16>(Qp, args, grid, block, smem, st);
+    case kStoreF16: return launch_q<StoreF16>(Qp, args, grid, block, smem, st);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t set_smem(int store_kind, size_t smem) {
+cudaError_t set_smem(int store_kind, int Qp, size_t smem) {
   switch (store_kind) {
-    case kStoreF64: return set_smem_one<StoreF64>(smem);
-    case kStoreF32: return set_smem_one<StoreF32>(smem);
-    case kStoreBF16: return set_smem_one<StoreBF16>(smem);
-    case kStoreF16: return set_smem_one<StoreF16>(smem);
+    case kStoreF64: return set_smem_q<StoreF64>(Qp, smem);
+    case kStoreF32: return set_smem_q<StoreF32>(Qp, smem);
+    case kStoreBF16: return set_smem_q<StoreBF16>(Qp, smem);
+    case kStoreF16: return set_smem_q<StoreF16>(Qp, smem);
   }
   return cudaErrorInvalidValue;
 }
@@ -570,6 +699,7 @@ StageEntry FEDBM_STAGE_ENTRY_NAME() {
   s.launch = &launch;
   s.set_smem = &set_smem;
   s.upload = &upload;
+  s.occupancy = &occupancy;
   return s;
 }
 

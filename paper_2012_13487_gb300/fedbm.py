@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
     _fields_ = [("kn", ctypes.c_double), ("length", ctypes.c_double), ("beta", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("reduction", ctypes.c_int32), ("collision", ctypes.c_int32),
-                ("elems_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32)]
+                ("elems_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
+                ("pipeline_stages", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -51,8 +52,14 @@ class Info(ctypes.Structure):
                 ("tau", ctypes.c_double), ("time", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("precision", ctypes.c_int32), ("reduction", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("eq_order", ctypes.c_int32), ("elems_per_cta", ctypes.c_int32),
-                ("threads_per_cta", ctypes.c_int32), ("state_bytes", ctypes.c_int64),
+                ("threads_per_cta", ctypes.c_int32), ("pipeline_stages", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("group", ctypes.c_int32), ("ngroups", ctypes.c_int32),
+                ("state_bytes", ctypes.c_int64),
                 ("residual_bytes", ctypes.c_int64)]
+
+
+class CaseDesc(ctypes.Structure):
+    _fields_ = [("mesh", MeshDesc), ("velset", VelsetDesc), ("params", Params)]
 
 
 _P = ctypes.c_void_p
@@ -82,6 +89,17 @@ SIGNATURES = {
     "fedbm_last_error": (ctypes.c_char_p, []),
     "fedbm_mass_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                           _P, _P, _P]),
+    "fedbm_batch_create": (ctypes.c_int, [ctypes.POINTER(CaseDesc), ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    "fedbm_batch_destroy": (None, [_P]),
+    "fedbm_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "fedbm_batch_set_equilibrium": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                                   ctypes.c_double, ctypes.c_double, ctypes.c_uint64]),
+    "fedbm_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "fedbm_batch_get_moments": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32]),
+    "fedbm_batch_mass": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
+    "fedbm_batch_info": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Info)]),
+    "fedbm_batch_rk_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "fedbm_batch_set_tiles": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
 }
 
 _lib = None
@@ -145,11 +163,12 @@ def velset_desc(kind=VELSET_GH, n=4, eq_order=2, nc_extent=4.0, nc_sqrt2=0):
 
 
 def params(kn=1.0, precision=FP32, reduction=RED_DEFAULT, cfl=0.5, dt=0.0, beta=1.0, collision=1,
-           length=1.0, elems_per_cta=0, threads_per_cta=0):
+           length=1.0, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0):
     p = Params()
     p.kn, p.length, p.beta, p.cfl, p.dt = kn, length, beta, cfl, dt
     p.precision, p.reduction, p.collision = precision, reduction, collision
     p.elems_per_cta, p.threads_per_cta = elems_per_cta, threads_per_cta
+    p.pipeline_stages = pipeline_stages
     return p
 
 
@@ -242,6 +261,108 @@ def fedbm_mass_noalloc(f, jac, mass_colsum, K, Np, Q, total, status, stream=0):
     """Allocation-free mass diagnostic on caller-owned device buffers (see the C header)."""
     _check(lib().fedbm_mass_noalloc(_ptr(f), _ptr(jac), _ptr(mass_colsum), K, Np, Q, _ptr(total),
                                     _ptr(status), ctypes.c_void_p(stream)))
+
+
+def fedbm_batch_create(cases, stream=0):
+    arr = (CaseDesc * len(cases))(*cases)
+    h = ctypes.c_void_p()
+    _check(lib().fedbm_batch_create(arr, len(cases), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def fedbm_batch_destroy(h):
+    lib().fedbm_batch_destroy(h)
+
+
+def fedbm_batch_set_state(h, c, f, on_device):
+    _check(lib().fedbm_batch_set_state(h, c, _ptr(f), int(on_device)))
+
+
+def fedbm_batch_set_equilibrium(h, c, rho0=1.0, ux0=0.0, uy0=0.0, amp=0.0, seed=0):
+    _check(lib().fedbm_batch_set_equilibrium(h, c, rho0, ux0, uy0, amp, seed))
+
+
+def fedbm_batch_get_state(h, c, f, on_device):
+    _check(lib().fedbm_batch_get_state(h, c, _ptr(f), int(on_device)))
+
+
+def fedbm_batch_get_moments(h, c, rho, ux, uy, on_device):
+    _check(lib().fedbm_batch_get_moments(h, c, _ptr(rho), _ptr(ux), _ptr(uy), int(on_device)))
+
+
+def fedbm_batch_mass(h, c):
+    m = ctypes.c_double()
+    _check(lib().fedbm_batch_mass(h, c, ctypes.byref(m)))
+    return m.value
+
+
+def fedbm_batch_info(h, c):
+    info = Info()
+    _check(lib().fedbm_batch_info(h, c, ctypes.byref(info)))
+    return info
+
+
+def fedbm_batch_rk_step(h, nsteps=1):
+    _check(lib().fedbm_batch_rk_step(h, nsteps))
+
+
+def fedbm_batch_set_tiles(h, group, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0):
+    _check(lib().fedbm_batch_set_tiles(h, group, elems_per_cta, threads_per_cta, pipeline_stages))
+
+
+def case_desc(mesh, vs, prm):
+    c = CaseDesc()
+    c.mesh, c.velset, c.params = mesh, vs, prm
+    return c
+
+
+class Batch:
+    """Owning handle of a batch of cases."""
+
+    def __init__(self, cases, stream=0):
+        self.h = fedbm_batch_create(cases, stream)
+        self.n = len(cases)
+
+    def info(self, c):
+        return fedbm_batch_info(self.h, c)
+
+    def shape(self, c):
+        i = fedbm_batch_info(self.h, c)
+        return (i.K, i.Np, i.Q)
+
+    def set_state(self, c, f, on_device=False):
+        fedbm_batch_set_state(self.h, c, f, on_device)
+
+    def set_equilibrium(self, c, rho0=1.0, ux0=0.0, uy0=0.0, amp=0.0, seed=0):
+        fedbm_batch_set_equilibrium(self.h, c, rho0, ux0, uy0, amp, seed)
+
+    def step(self, n=1):
+        fedbm_batch_rk_step(self.h, n)
+
+    def state(self, c):
+        f = np.zeros(self.shape(c))
+        fedbm_batch_get_state(self.h, c, f, False)
+        return f
+
+    def moments(self, c):
+        K, Np, _ = self.shape(c)
+        rho, ux, uy = np.zeros((K, Np)), np.zeros((K, Np)), np.zeros((K, Np))
+        fedbm_batch_get_moments(self.h, c, rho, ux, uy, False)
+        return rho, ux, uy
+
+    def mass(self, c):
+        return fedbm_batch_mass(self.h, c)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            fedbm_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

@@ -28,7 +28,8 @@ def oracle_problem(c):
                       nc_scale=np.sqrt(2.0) if c.get("nc_sqrt2", False) else 1.0)
 
 
-def solver(c, precision="fp32", reduction="default", **tile):
+def descriptors(c, precision="fp32", reduction="default", **tile):
+    """(mesh, velset, params) descriptors of a case dict for the C ABI."""
     from paper_2012_13487_gb300 import fedbm as fb
     vs = c.get("velset", ("gh", 4))
     m = fb.mesh_desc(c["nx"], c["ny"], c["p"], bc=tuple(BC_CODE[b] for b in c["bc"]), wall_u=c["wall_u"])
@@ -36,8 +37,19 @@ def solver(c, precision="fp32", reduction="default", **tile):
                        nc_sqrt2=int(c.get("nc_sqrt2", False)))
     prm = fb.params(kn=c.get("kn", 1.0), precision=PREC_CODE[precision], reduction=RED_CODE[reduction],
                     cfl=c.get("cfl", 0.5), beta=c.get("beta", 1.0), collision=int(c.get("collision", True)),
-                    elems_per_cta=tile.get("epc", 0), threads_per_cta=tile.get("tpb", 0))
-    return fb.Solver(m, v, prm)
+                    elems_per_cta=tile.get("epc", 0), threads_per_cta=tile.get("tpb", 0),
+                    pipeline_stages=tile.get("stages", 0))
+    return m, v, prm
+
+
+def solver(c, precision="fp32", reduction="default", **tile):
+    from paper_2012_13487_gb300 import fedbm as fb
+    return fb.Solver(*descriptors(c, precision, reduction, **tile))
+
+
+def batch(cs, precision="fp32", reduction="default", **tile):
+    from paper_2012_13487_gb300 import fedbm as fb
+    return fb.Batch([fb.case_desc(*descriptors(c, precision, reduction, **tile)) for c in cs])
 
 
 def initial_state(pr, amp=1e-3, seed=201213487, rho0=1.0, ux0=0.0, uy0=0.0):

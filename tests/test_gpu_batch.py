@@ -1,0 +1,56 @@
+"""GPU tests of the batched form: many independent Couette and cavity cases of
+uneven mesh size, degree, velocity set, Kn and wall speed advance together."""
+import numpy as np
+import pytest
+
+import cases
+from test_gpu_parity import fp32_tol
+
+pytestmark = pytest.mark.gpu
+
+
+MIX = [
+    cases.couette(3, 4, 2, U=0.05, velset=("gh", 4), kn=0.7),
+    cases.cavity(4, 3, 3, U=0.2, velset=("nc", 16), kn=8.0),
+    cases.cavity(2, 5, 2, U=0.1, velset=("gh", 4), kn=2.0),      # same group as case 0
+    cases.couette(5, 2, 3, U=0.15, velset=("nc", 16), kn=0.5),    # same group as case 1
+    cases.cavity(3, 3, 4, U=0.12, velset=("gh", 4), kn=1.3),
+    cases.couette(2, 2, 5, U=0.08, velset=("gh", 4), kn=4.0),
+]
+
+
+def test_batch_matches_oracle_and_single_solvers():
+    b = cases.batch(MIX, "fp32")
+    groups = {b.info(c).group for c in range(len(MIX))}
+    assert b.info(0).ngroups == len(groups) == 4
+    assert b.info(0).group == b.info(2).group and b.info(1).group == b.info(3).group
+    prs, f0s = [], []
+    for c, case in enumerate(MIX):
+        pr = cases.oracle_problem(case)
+        f0 = cases.initial_state(pr, amp=0.05, seed=100 + c)
+        b.set_state(c, f0)
+        prs.append(pr)
+        f0s.append(f0)
+    nsteps = 6
+    b.step(nsteps)
+    for c, case in enumerate(MIX):
+        pr, f0 = prs[c], f0s[c]
+        assert b.info(c).dt == pytest.approx(pr.dt, rel=1e-14)
+        got = b.state(c)
+        want = pr.run(f0, nsteps)
+        assert cases.rel_max_err(got, want) <= fp32_tol(pr, 5 * nsteps)
+        single = cases.solver(case, "fp32")
+        single.set_state(f0)
+        single.step(nsteps)
+        np.testing.assert_array_equal(got, single.state())   # same arithmetic per element
+
+
+def test_batch_equilibrium_and_mass_per_case():
+    b = cases.batch(MIX[:3], "fp32")
+    for c in range(3):
+        b.set_equilibrium(c, 1.0, 0.0, 0.0, 1e-3, 7 + c)
+    m0 = [b.mass(c) for c in range(3)]
+    b.step(20)
+    for c in range(3):
+        # diffuse walls conserve mass; FP32 state rounding bounds the drift
+        assert abs(b.mass(c) - m0[c]) < 1e-5 * abs(m0[c])

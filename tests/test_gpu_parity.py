@@ -78,12 +78,33 @@ def test_fp32_parity(c):
     assert err <= fp32_tol(pr, 5 * n), (err, fp32_tol(pr, 5 * n))
 
 
-@pytest.mark.parametrize("epc,tpb", [(1, 32), (3, 64), (8, 128), (16, 256), (5, 96)])
-def test_fp32_tile_shapes_agree(epc, tpb):
+@pytest.mark.parametrize("epc,tpb,stages", [(1, 32, 1), (3, 64, 2), (8, 128, 1), (16, 256, 2), (5, 96, 2),
+                                            (1, 32, 2)])
+def test_fp32_tile_shapes_agree(epc, tpb, stages):
     c = cases.cavity(5, 4, 3, velset=("gh", 4), kn=1.0)
-    pr, s, f0, f_gpu, f_or = _run_pair(c, 4, "fp32", amp=0.05, epc=epc, tpb=tpb)
+    pr, s, f0, f_gpu, f_or = _run_pair(c, 4, "fp32", amp=0.05, epc=epc, tpb=tpb, stages=stages)
     assert s.info.elems_per_cta == epc and s.info.threads_per_cta == tpb
+    assert s.info.pipeline_stages == stages
     assert cases.rel_max_err(f_gpu, f_or) <= fp32_tol(pr, 20)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_pipelined_persistent_tiles(prec):
+    """Two tile buffers per CTA and fewer CTAs than tiles: each CTA loops over
+    several tiles, loading the next one while it computes the current one."""
+    n = 16 if prec == "fp32" else 24          # enough tiles to exceed one wave of CTAs
+    c = cases.cavity(n, n, 3, velset=("nc", 16), kn=8.0)
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=0.05)
+    ref = cases.solver(c, prec, stages=1, epc=1, tpb=256)
+    s = cases.solver(c, prec, stages=2, epc=1, tpb=256)
+    assert s.info.pipeline_stages == 2 and s.info.grid < s.info.K
+    for x in (ref, s):
+        x.set_state(f0)
+        x.step(3)
+    np.testing.assert_array_equal(s.state(), ref.state())   # same arithmetic, other schedule
+    if prec == "fp32":
+        assert cases.rel_max_err(s.state(), pr.run(f0, 3)) <= fp32_tol(pr, 15)
 
 
 @pytest.mark.parametrize("red", ["fp64", "comp"])
