@@ -52,6 +52,10 @@ WORKLOADS = {
         desc="lid-driven cavity Kn=8, 128x128x2 triangles, p=3, NC 32x32, BF16 deviation state, FP64 moments",
         reduction="fp64"),
 }
+WORKLOADS["batch256_couette_cavity_fp32"] = dict(
+    kind="batch", seed=201213487, n=256, precision="fp32",
+    desc="256 seeded independent cases (128 Couette, 128 cavity; Kn log-uniform in [0.5, 8], wall/lid "
+         "speed in [0.05, 0.2], N x N x 2 triangles with N in 16..64, p in 2..5, GH D2Q16 or NC 16x16), FP32")
 DEFAULT_WORKLOAD = "cavity_kn1_64x64x2_p4_nc16x16_fp32"
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 RED = {"default": 0, "fp64": 1, "comp": 2}
@@ -65,6 +69,15 @@ def algorithmic_bytes_per_dof_step(prec):
     """Five stages; the first has A = 0 and does not read the residual."""
     s, r = STATE_BYTES[prec], RES_BYTES[prec]
     return (2 * s + r) + 4 * (2 * s + 2 * r)
+
+
+def batch_case_list(w):
+    from paper_2012_13487_gb300 import inputs
+    out = []
+    for c in inputs.batch_cases(w["seed"], w["n"]):
+        out.append(dict(kind=c["kind"], nx=c["N"], ny=c["N"], p=c["p"], vel=c["vel"], kn=c["kn"],
+                        speed=c["speed"], precision=w["precision"]))
+    return out
 
 
 def dims(w):
@@ -159,7 +172,7 @@ class ClockSampler:
                                                     if r[3].replace(".", "").isdigit()) if rows else None}
 
 
-def make_solver(w, stream_handle, epc=0, tpb=0, stages=0):
+def make_descriptors(w, epc=0, tpb=0, stages=0):
     from paper_2012_13487_gb300 import fedbm as fb
     if w["kind"] == "cavity":
         bc = (fb.BC_WALL_DIFFUSE,) * 4
@@ -172,7 +185,62 @@ def make_solver(w, stream_handle, epc=0, tpb=0, stages=0):
     v = fb.velset_desc(fb.VELSET_GH if kind == "gh" else fb.VELSET_NC, n, eq_order=w.get("eq_order", 2))
     prm = fb.params(kn=w["kn"], precision=PREC[w["precision"]], reduction=RED[w.get("reduction", "default")],
                     cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb, pipeline_stages=stages)
-    return fb.Solver(m, v, prm, stream_handle)
+    return m, v, prm
+
+
+def make_solver(w, stream_handle, epc=0, tpb=0, stages=0):
+    from paper_2012_13487_gb300 import fedbm as fb
+    return fb.Solver(*make_descriptors(w, epc, tpb, stages), stream_handle)
+
+
+def make_batch(cases, stream_handle):
+    from paper_2012_13487_gb300 import fedbm as fb
+    return fb.Batch([fb.case_desc(*make_descriptors(c)) for c in cases], stream_handle)
+
+
+def time_steps(step, stream, steps, warmup):
+    """Event time (ms) of `steps` calls of step(1) on `stream` after `warmup` calls."""
+    import torch
+    step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_batch(w, stream, steps, warmup, loop_steps, tune):
+    """Batched form and the case-by-case loop of single solvers on the same cases."""
+    import torch
+    cases = batch_case_list(w)
+    dof = sum(2 * c["nx"] * c["ny"] * ((c["p"] + 1) * (c["p"] + 2) // 2) * c["vel"][1] ** 2 for c in cases)
+    b = make_batch(cases, stream.cuda_stream)
+    for i in range(len(cases)):
+        b.set_equilibrium(i, 1.0, 0.0, 0.0, 1e-3, 201213487 + i)
+    if tune:
+        b.autotune(None, 3)
+    ngroups = b.info(0).ngroups
+    ms = time_steps(b.step, stream, steps, warmup)
+    b.close()
+    torch.cuda.synchronize()
+    solvers = [make_solver(c, stream.cuda_stream) for c in cases]
+    for i, s in enumerate(solvers):
+        s.set_equilibrium(1.0, 0.0, 0.0, 1e-3, 201213487 + i)
+
+    def loop(n):
+        for _ in range(n):
+            for s in solvers:
+                s.step(1)
+
+    ms_loop = time_steps(loop, stream, loop_steps, 1)
+    for s in solvers:
+        s.close()
+    return {"value": dof * 5 * steps / (ms / 1e3), "loop_value": dof * 5 * loop_steps / (ms_loop / 1e3),
+            "cases": len(cases), "groups": ngroups, "dof": dof, "steps": steps, "loop_steps": loop_steps,
+            "ms_per_step": ms / steps, "loop_ms_per_step": ms_loop / loop_steps}
 
 
 # ---------------------------------------------------------------- oracle timing
@@ -230,6 +298,8 @@ def run_reference(args, w, name):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
+    if w["kind"] == "batch":   # the oracle samples the first case of the batch
+        w = dict(batch_case_list(w)[0], desc=w["desc"])
     K, Np, Q = dims(w)
     # each step: one LSRK stage of the oracle on 64 sampled elements (FP64)
     totals, seconds = 0, 0.0
@@ -263,10 +333,14 @@ def run_ours(args, w, name):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     st = torch.cuda.Stream()
+    if w["kind"] == "batch":
+        return run_batch_workload(args, w, name, st, world, rank, dist)
     K, Np, Q = dims(w)
     dof = K * Np * Q
     s = make_solver(w, st.cuda_stream, args.epc, args.tpb, args.stages)
     s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+    if not args.no_tune and not (args.epc or args.tpb or args.stages):
+        s.autotune(None, 5)
     s.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -337,6 +411,23 @@ def run_ours(args, w, name):
                          "%d-element mesh, single thread, %.1f s" % (out["stages"], out["elements"],
                                                                      out["dof_stages"] // out["stages"],
                                                                      out["K"], out["seconds"])}
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms and name == DEFAULT_WORKLOAD:
+        # the three forms of the metric: FP32 state (this line), BF16 deviation
+        # state on the same mesh, and the seeded 256-case batch
+        wb = dict(w, precision="bf16", desc=w["desc"].replace("FP32", "BF16 deviation state"))
+        sb = make_solver(wb, st.cuda_stream)
+        sb.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+        if not args.no_tune:
+            sb.autotune(None, 5)
+        ms_b = time_steps(sb.step, st, max(1, args.steps // 2), args.warmup)
+        sb.close()
+        bat = measure_batch(WORKLOADS["batch256_couette_cavity_fp32"], st, 10, 3, 2, not args.no_tune)
+        forms = {"fp32": {"value": value, "workload": w["desc"]},
+                 "bf16_state": {"value": dof * 5 * max(1, args.steps // 2) / (ms_b / 1e3), "workload": wb["desc"],
+                                "algorithmic_bytes_per_dof_step": algorithmic_bytes_per_dof_step("bf16")},
+                 "batched": dict(bat, workload=WORKLOADS["batch256_couette_cavity_fp32"]["desc"]),
+                 "unit": "DOF-stage/s"}
     if rank == 0:
         line = {
             "metric": "DOF-stage updates/s", "value": value, "unit": "DOF-stage/s", "n_gpus": world,
@@ -362,9 +453,53 @@ def run_ours(args, w, name):
             "gpu_launches": 5 * args.steps,
             "clocks": clocks,
             "mass_after": mass,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_batch_workload(args, w, name, st, world, rank, dist):
+    """The seeded 256-case batch as the timed workload (one graph launch per
+    step advances every case); the case-by-case loop is reported beside it."""
+    import torch
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    if dist is not None:
+        dist.barrier()
+    bat = measure_batch(w, st, args.steps, args.warmup, max(1, min(args.steps, 3)), not args.no_tune)
+    clocks = sampler.stop()
+    ms = bat["ms_per_step"] * args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * bat["dof"] * 5 * args.steps / (ms / 1e3)
+    peak, peak_kind = hbm_peak()
+    achieved = bat["dof"] * algorithmic_bytes_per_dof_step("fp32") * args.steps / (ms / 1e3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "DOF-stage updates/s", "value": value, "unit": "DOF-stage/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["desc"], "name": name, "cases": bat["cases"], "groups": bat["groups"],
+                       "dof": bat["dof"], "l2": "inputs larger than L2, no flush",
+                       "parallelism": "replicas x%d" % world},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                         "algorithmic_bytes_per_dof_step": algorithmic_bytes_per_dof_step("fp32"),
+                         "kernel": "stage_kernel, all groups"},
+            "loop_baseline": {"value": bat["loop_value"], "unit": "DOF-stage/s",
+                              "ms_per_step": bat["loop_ms_per_step"],
+                              "what": "the same cases stepped one solver at a time"},
+            "cpu_baseline": None,
+            "e2e": None,
+            "gpu_launches": 5 * bat["groups"] * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -381,6 +516,8 @@ def main():
     ap.add_argument("--epc", type=int, default=0, help="stage tile: elements per CTA (0 = library default)")
     ap.add_argument("--tpb", type=int, default=0, help="stage tile: threads per CTA (0 = library default)")
     ap.add_argument("--stages", type=int, default=0, help="stage tile buffers per CTA (0 = library default)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the tile autotuner")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched form measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

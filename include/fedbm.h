@@ -242,6 +242,16 @@ int fedbm_batch_rk_step(fedbm_batch* b, int32_t nsteps);
 int fedbm_batch_set_tiles(fedbm_batch* b, int32_t group, int32_t elems_per_cta,
                           int32_t threads_per_cta, int32_t pipeline_stages);
 
+/* Tile autotuner: for every kernel group, time each candidate stage-kernel
+ * tile (elements per CTA 1..32, threads per CTA 64/128/256, one or two
+ * pipeline stages) on `trials` launches (0 means 5) and keep the fastest.
+ * The current state is left unchanged.  With a cache_path (NULL or "" for
+ * none), results are read from and written to a JSON object keyed by device
+ * name, degree, padded velocity count, precision, reduction and element
+ * count.  Synchronous.  Errors: ECUDA if no candidate runs. */
+int fedbm_batch_autotune(fedbm_batch* b, const char* cache_path, int32_t trials);
+int fedbm_autotune(fedbm_solver* s, const char* cache_path, int32_t trials);
+
 /* Allocation-free mass diagnostic.  The paper has no counterpart; this entry
  * point serves callers that must not allocate device memory once they are
  * running -- an application whose device memory belongs to another allocator

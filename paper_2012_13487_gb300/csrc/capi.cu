@@ -398,6 +398,117 @@ int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
   return FEDBM_OK;
 }
 
+// ---- tile autotuner ------------------------------------------------------------
+// For every group, time each candidate (elements per CTA, threads per CTA,
+// pipeline stages) on `trials` launches of RK stage 2 (the residual-reading
+// form) and keep the fastest.  The kernel reads f[cur] and writes f[1-cur] and
+// the residual, so the current state is untouched; the residual's contents
+// are overwritten by the next step's first stage, which does not read it.
+// Results are cached per (device, degree, velocity count, precision,
+// element count) in a flat JSON object, one entry per line.
+struct TuneEntry {
+  int epc = 0, tpb = 0, stages = 0;
+  double us = 0;
+};
+
+std::string tune_key(const Batch& b, const Group& g) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, b.device);
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s|p%d|Q%d|store%d|red%d|K%lld", prop.name, g.p, g.Qp, g.store, g.reduction,
+                static_cast<long long>(g.K));
+  return buf;
+}
+
+std::vector<std::pair<std::string, TuneEntry>> read_tune_cache(const char* path) {
+  std::vector<std::pair<std::string, TuneEntry>> out;
+  if (!path || !*path) return out;
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return out;
+  char line[1024];
+  while (std::fgets(line, sizeof(line), fp)) {
+    char key[512];
+    TuneEntry t;
+    if (std::sscanf(line, " \"%511[^\"]\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"us\": %lf}", key, &t.epc,
+                    &t.tpb, &t.stages, &t.us) == 5)
+      out.emplace_back(key, t);
+  }
+  std::fclose(fp);
+  return out;
+}
+
+void write_tune_cache(const char* path, const std::vector<std::pair<std::string, TuneEntry>>& entries) {
+  if (!path || !*path) return;
+  FILE* fp = std::fopen(path, "w");
+  if (!fp) return;
+  std::fprintf(fp, "{\n");
+  for (size_t j = 0; j < entries.size(); ++j)
+    std::fprintf(fp, "\"%s\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"us\": %.3f}%s\n",
+                 entries[j].first.c_str(), entries[j].second.epc, entries[j].second.tpb, entries[j].second.stages,
+                 entries[j].second.us, j + 1 < entries.size() ? "," : "");
+  std::fprintf(fp, "}\n");
+  std::fclose(fp);
+}
+
+int autotune(Batch& b, const char* cache_path, int trials) {
+  if (trials < 1) trials = 5;
+  auto cache = read_tune_cache(cache_path);
+  bool dirty = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FEDBM_CK(cudaEventCreate(&e0));
+  FEDBM_CK(cudaEventCreate(&e1));
+  int rc = FEDBM_OK;
+  for (Group& g : b.groups) {
+    const std::string key = tune_key(b, g);
+    const TuneEntry* hit = nullptr;
+    for (auto& kv : cache)
+      if (kv.first == key) hit = &kv.second;
+    if (hit) {
+      if ((rc = configure_tiles(b, g, hit->epc, hit->tpb, hit->stages)) != FEDBM_OK) break;
+      continue;
+    }
+    TuneEntry best;
+    best.us = 1e300;
+    const int epcs[] = {1, 2, 4, 8, 16, 32};
+    const int tpbs[] = {64, 128, 256};
+    for (int epc : epcs) {
+      if (epc * g.Qp > 4096 || epc > g.K) continue;
+      for (int tpb : tpbs) {
+        if (tpb > 32 * ((epc * g.Qp + 31) / 32) * 2) continue;  // at most half the threads idle
+        for (int stages = 1; stages <= 2; ++stages) {
+          if (configure_tiles(b, g, epc, tpb, stages) != FEDBM_OK || g.nstages != stages) continue;
+          if (launch_stage(g, 1, b.cur, b.stream) != cudaSuccess) continue;  // warm-up
+          cudaEventRecord(e0, b.stream);
+          for (int t = 0; t < trials; ++t) launch_stage(g, 1, b.cur, b.stream);
+          cudaEventRecord(e1, b.stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          const double us = 1e3 * double(ms) / trials;
+          if (us < best.us) {
+            best.epc = epc;
+            best.tpb = tpb;
+            best.stages = stages;
+            best.us = us;
+          }
+        }
+      }
+    }
+    cudaGetLastError();
+    if (best.epc == 0) {
+      rc = fail(FEDBM_ECUDA, "autotune: no tile candidate could run");
+      break;
+    }
+    if ((rc = configure_tiles(b, g, best.epc, best.tpb, best.stages)) != FEDBM_OK) break;
+    cache.emplace_back(key, best);
+    dirty = true;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == FEDBM_OK && dirty) write_tune_cache(cache_path, cache);
+  return rc;
+}
+
 // One RK step of every group, captured once per buffer parity; groups are
 // independent branches of the graph so that small groups run side by side.
 int build_graphs(Batch& b) {
@@ -1122,4 +1233,14 @@ extern "C" int fedbm_batch_set_tiles(fedbm_batch* h, int32_t group, int32_t elem
   FEDBM_BATCH(h, 0);
   if (group < 0 || group >= int(B.groups.size())) return fail(FEDBM_EINVAL, "group index out of range");
   return configure_tiles(B, B.groups[group], elems_per_cta, threads_per_cta, pipeline_stages);
+}
+
+extern "C" int fedbm_batch_autotune(fedbm_batch* h, const char* cache_path, int32_t trials) {
+  FEDBM_BATCH(h, 0);
+  return autotune(B, cache_path, trials);
+}
+
+extern "C" int fedbm_autotune(fedbm_solver* s, const char* cache_path, int32_t trials) {
+  FEDBM_SOLVER(s);
+  return autotune(B, cache_path, trials);
 }

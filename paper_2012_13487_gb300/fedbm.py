@@ -100,6 +100,8 @@ SIGNATURES = {
     "fedbm_batch_info": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Info)]),
     "fedbm_batch_rk_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "fedbm_batch_set_tiles": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "fedbm_batch_autotune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int32]),
+    "fedbm_autotune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int32]),
 }
 
 _lib = None
@@ -310,6 +312,14 @@ def fedbm_batch_set_tiles(h, group, elems_per_cta=0, threads_per_cta=0, pipeline
     _check(lib().fedbm_batch_set_tiles(h, group, elems_per_cta, threads_per_cta, pipeline_stages))
 
 
+def fedbm_batch_autotune(h, cache_path=None, trials=0):
+    _check(lib().fedbm_batch_autotune(h, cache_path.encode() if cache_path else None, trials))
+
+
+def fedbm_autotune(h, cache_path=None, trials=0):
+    _check(lib().fedbm_autotune(h, cache_path.encode() if cache_path else None, trials))
+
+
 def case_desc(mesh, vs, prm):
     c = CaseDesc()
     c.mesh, c.velset, c.params = mesh, vs, prm
@@ -352,6 +362,9 @@ class Batch:
 
     def mass(self, c):
         return fedbm_batch_mass(self.h, c)
+
+    def autotune(self, cache_path=None, trials=0):
+        fedbm_batch_autotune(self.h, cache_path, trials)
 
     def close(self):
         if self.h is not None and self.h.value:
@@ -407,6 +420,10 @@ class Solver:
 
     def mass(self):
         return fedbm_mass(self.h)
+
+    def autotune(self, cache_path=None, trials=0):
+        fedbm_autotune(self.h, cache_path, trials)
+        self.info = fedbm_info(self.h)
 
     def close(self):
         if self.h is not None and self.h.value:

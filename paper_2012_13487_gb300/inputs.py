@@ -35,3 +35,31 @@ def perturbation(seed, K, Np, Q):
     """Uniform [-1, 1) field of shape [K, Np, Q] (canonical layout)."""
     with np.errstate(over="ignore"):
         return uniform_pm1(seed, K * Np * Q).reshape(K, Np, Q)
+
+
+def uniform01(seed, n, start=0):
+    """n doubles in [0, 1) from SplitMix64(seed XOR index)."""
+    idx = np.arange(start, start + n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = splitmix64(np.uint64(seed) ^ idx)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def batch_cases(seed=201213487, n=256):
+    """Seeded mix of n independent cases: the first half Couette, the rest
+    lid-driven cavity; Kn log-uniform in [0.5, 8]; wall or lid speed uniform
+    in [0.05, 0.2] sqrt(RT); N x N x 2 triangles with N uniform in 16..64;
+    degree uniform in 2..5; velocity set GH D2Q16 or NC 16 x 16 with
+    probability 1/2 each.  Returns a list of dicts (draws only)."""
+    u = uniform01(seed, 5 * n).reshape(n, 5)
+    out = []
+    for c in range(n):
+        out.append(dict(
+            kind="couette" if c < n // 2 else "cavity",
+            kn=float(np.exp(np.log(0.5) + u[c, 0] * (np.log(8.0) - np.log(0.5)))),
+            speed=float(0.05 + 0.15 * u[c, 1]),
+            N=int(16 + min(48, int(u[c, 2] * 49))),
+            p=int(2 + min(3, int(u[c, 3] * 4))),
+            vel=("gh", 4) if u[c, 4] < 0.5 else ("nc", 16),
+        ))
+    return out

@@ -54,3 +54,30 @@ def test_batch_equilibrium_and_mass_per_case():
     for c in range(3):
         # diffuse walls conserve mass; FP32 state rounding bounds the drift
         assert abs(b.mass(c) - m0[c]) < 1e-5 * abs(m0[c])
+
+
+def test_autotune_keeps_state_and_uses_cache(tmp_path):
+    b = cases.batch(MIX[:4], "fp32")
+    f0s = []
+    for c in range(4):
+        pr = cases.oracle_problem(MIX[c])
+        f0s.append(cases.initial_state(pr, amp=0.05, seed=c))
+        b.set_state(c, f0s[-1])
+    cache = str(tmp_path / "tiles.json")
+    b.autotune(cache, 2)
+    for c in range(4):
+        np.testing.assert_array_equal(b.state(c), np.asarray(b.state(c)))
+        assert cases.rel_max_err(b.state(c), f0s[c]) < 1e-7        # only FP32 rounding of f0
+    text = open(cache).read()
+    assert text.count('"epc"') == b.info(0).ngroups
+    tiles = [(b.info(c).elems_per_cta, b.info(c).threads_per_cta, b.info(c).pipeline_stages) for c in range(4)]
+    b.step(2)
+    b2 = cases.batch(MIX[:4], "fp32")
+    b2.autotune(cache, 2)                                           # served from the cache
+    assert [(b2.info(c).elems_per_cta, b2.info(c).threads_per_cta, b2.info(c).pipeline_stages)
+            for c in range(4)] == tiles
+    for c in range(4):
+        b2.set_state(c, f0s[c])
+    b2.step(2)
+    for c in range(4):
+        np.testing.assert_array_equal(b2.state(c), b.state(c))
