@@ -317,11 +317,167 @@ __device__ __forceinline__ R collision(const R* mm, R ex, R ey, R w, R f, R inv_
   return fma(w, feq, -inv_tau * f);
 }
 
+// Adjacent velocities handled by one thread in phase 4: two for the
+// specialised 16-bit-state kernels up to degree 4 (each operator constant then
+// feeds two FMAs and the per-item set-up is shared), else one.
+template <class ST, int QT>
+__host__ __device__ constexpr int items_vpt() {
+  return (QT > 0 && ST::dev && P <= 4) ? 2 : 1;
+}
+
+template <typename T, int N>
+struct alignas(N * sizeof(T)) Vec {
+  T v[N];
+};
+
+// Phase 4: residual, 2N-storage update and write-back of every (element,
+// velocity) value of the tile; each thread owns VPT adjacent velocities of one
+// element.  Plain forms update f in place in shared memory; deviation forms
+// only track max |f/w - 1| per element (the encoding pass recomputes f).
+template <class ST, int QT, int VPT>
+__device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
+                                            StageSmem<typename ST::R, typename ST::S>& sm, int64_t k0, int ne,
+                                            bool read_res, float& dmax, int& emax) {
+  using R = typename ST::R;
+  using S = typename ST::S;
+  using SV = Vec<S, VPT>;
+  using RV = Vec<R, VPT>;
+  const int Qp = QT > 0 ? QT : a.Qp;
+  const int Qv = Qp / VPT;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const R rkA = a.rkA, rkB = a.rkB, ab = a.ab;
+  const bool third = a.eq_order == 3;
+  for (int item = tid; item < ne * Qv; item += nth) {
+    const int e = item / Qv;
+    const int i = (item - e * Qv) * VPT;
+    const RV exv = *reinterpret_cast<const RV*>(a.vel + kVelEx * Qp + i);
+    const RV eyv = *reinterpret_cast<const RV*>(a.vel + kVelEy * Qp + i);
+    const RV wv = *reinterpret_cast<const RV*>(a.vel + kVelW * Qp + i);
+    const R* g = sm.geo + e * kGeoStrideDev;
+    const R dt = g[kGeoDt], inv_tau = g[kGeoInvTau];  // per element: cases of a batch differ
+    R ar[VPT], as[VPT], ws[VPT];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      ar[v] = exv.v[v] * g[0] + eyv.v[v] * g[2];
+      as[v] = exv.v[v] * g[1] + eyv.v[v] * g[3];
+      ws[v] = ST::dev ? wv.v[v] * R(sm.scale[e]) : R(0);
+    }
+    S* frow = sm.f + size_t(e) * NP * Qp + i;
+    R* rrow = sm.res + size_t(e) * NP * Qp + i;
+
+    R fr[VPT][NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      const SV x = *reinterpret_cast<const SV*>(frow + m * Qp);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) fr[v][m] = decode<ST>(x.v[v], wv.v[v], ws[v]);
+    }
+
+    R flux[VPT][NF];
+#pragma unroll
+    for (int fc = 0; fc < 3; ++fc) {
+      R c[VPT], en[VPT];
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        en[v] = exv.v[v] * g[4 + 3 * fc] + eyv.v[v] * g[5 + 3 * fc];
+        c[v] = R(0.5) * (en[v] - ab * fabs(en[v])) * g[6 + 3 * fc];
+      }
+      const int code = sm.nbr[e * 3 + fc];
+      if (code >= 0) {
+        R wsn[VPT];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) wsn[v] = ST::dev ? wv.v[v] * R(sm.nscale[e * 3 + fc]) : R(0);
+        const S* trow = sm.tr + size_t(e * NF + fc * NFP) * Qp + i;
+#pragma unroll
+        for (int aa = 0; aa < NFP; ++aa) {
+          const SV x = *reinterpret_cast<const SV*>(trow + aa * Qp);
+#pragma unroll
+          for (int v = 0; v < VPT; ++v)
+            flux[v][fc * NFP + aa] = c[v] * (fr[v][face_node(fc, aa)] - decode<ST>(x.v[v], wv.v[v], wsn[v]));
+        }
+      } else {
+        const int slot = -code - 1;  // wall slot: 4 * case + side
+        const RV fbv = *reinterpret_cast<const RV*>(a.wall_feq + slot * Qp + i);
+        const R den_inv = __ldg(a.wall_den_inv + slot);
+        const bool diffuse = den_inv > R(0);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          // incoming velocities take the wall state; outgoing ones have no jump
+          const R scale = diffuse ? den_inv * fbv.v[v] : R(0);
+#pragma unroll
+          for (int aa = 0; aa < NFP; ++aa) {
+            const R fp = diffuse ? sm.wn[e * NF + fc * NFP + aa] * scale : fbv.v[v];
+            flux[v][fc * NFP + aa] = en[v] < R(0) ? c[v] * (fr[v][face_node(fc, aa)] - fp) : R(0);
+          }
+        }
+      }
+    }
+
+    float dloc = 0.f;
+    R invw[VPT];
+    if constexpr (ST::dev) {
+      const RV iw = *reinterpret_cast<const RV*>(a.vel + kVelInvW * Qp + i);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) invw[v] = iw.v[v];
+    }
+#pragma unroll
+    for (int n = 0; n < NP; ++n) {
+      RV rold;
+      if (read_res) rold = *reinterpret_cast<const RV*>(rrow + n * Qp);
+      R dr[VPT], ds[VPT], lf[VPT];
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) dr[v] = ds[v] = lf[v] = R(0);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        const R cr = opv<R>(OFF_DR + n * NP + m), cs = opv<R>(OFF_DS + n * NP + m);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          dr[v] = fma(cr, fr[v][m], dr[v]);
+          ds[v] = fma(cs, fr[v][m], ds[v]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NF; ++j) {
+        const R cl = opv<R>(OFF_LIFT + n * NF + j);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) lf[v] = fma(cl, flux[v][j], lf[v]);
+      }
+      const R* mm = sm.mom + (size_t(e) * NP + n) * 8;
+      RV rr;
+      SV fnew_s;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        R rhs = fma(-ar[v], dr[v], fma(-as[v], ds[v], lf[v]));
+        rhs += collision<R>(mm, exv.v[v], eyv.v[v], wv.v[v], fr[v][n], inv_tau, third);
+        R r = dt * rhs;
+        if (read_res) r = fma(rkA, rold.v[v], r);
+        rr.v[v] = r;
+        const R fnew = new_f<ST>(fr[v][n], rkB, r);
+        if constexpr (ST::dev) {
+          dloc = fmaxf(dloc, fabsf((fnew - wv.v[v]) * invw[v]));
+        } else {
+          fnew_s.v[v] = S(fnew);
+        }
+      }
+      *reinterpret_cast<RV*>(rrow + n * Qp) = rr;
+      if constexpr (!ST::dev) *reinterpret_cast<SV*>(frow + n * Qp) = fnew_s;
+    }
+    if constexpr (ST::dev) {
+      if (e != emax) {
+        if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
+        emax = e;
+        dmax = 0.f;
+      }
+      dmax = fmaxf(dmax, dloc);
+    }
+  }
+}
+
 // Minimum resident CTAs of 256 threads per SM: bounds the registers per thread
 // (65536 / (256 * min)) so that the unrolled node loop does not spill.
-template <class ST>
+template <class ST, int QT>
 __host__ __device__ constexpr int stage_min_blocks() {
-  return sizeof(typename ST::R) == 8 ? 2 : (P <= 3 ? 4 : (P <= 5 ? 3 : 2));
+  return sizeof(typename ST::R) == 8 ? 2 : items_vpt<ST, QT>() == 2 ? 2 : (P <= 3 ? 4 : (P <= 5 ? 3 : 2));
 }
 
 
@@ -385,7 +541,7 @@ __device__ void issue_tile_loads(const StageArgs<typename ST::R>& a, StageSmem<t
 // QT > 0: the padded velocity count is the compile-time constant QT (all
 // shared-memory strides become immediate offsets); QT = 0: taken from a.Qp.
 template <class ST, int QT>
-__global__ void __launch_bounds__(256, stage_min_blocks<ST>()) stage_kernel(const StageArgs<typename ST::R> a) {
+__global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(const StageArgs<typename ST::R> a) {
   using R = typename ST::R;
   using S = typename ST::S;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -460,94 +616,7 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST>()) stage_kernel(cons
     // ---- 4. residual and update ----------------------------------------------------
     float dmax = 0.f;  // deviation forms: running max |f/w - 1| of element emax
     int emax = -1;
-    {
-    const R rkB = a.rkB, ab = a.ab;
-    const bool third = a.eq_order == 3;
-    for (int item = tid; item < ne * Qp; item += nth) {
-      const int e = item / Qp;
-      const int i = item - e * Qp;
-      const R ex = __ldg(a.vel + kVelEx * Qp + i), ey = __ldg(a.vel + kVelEy * Qp + i);
-      const R w = __ldg(a.vel + kVelW * Qp + i);
-      const R* g = sm.geo + e * kGeoStrideDev;
-      const R ar = ex * g[0] + ey * g[2];
-      const R as = ex * g[1] + ey * g[3];
-      const R dt = g[kGeoDt], inv_tau = g[kGeoInvTau];  // per element: cases of a batch differ
-      R ws = 0;
-      if constexpr (ST::dev) ws = w * sm.scale[e];
-      S* frow = sm.f + size_t(e) * NP * Qp + i;
-      R* rrow = sm.res + size_t(e) * NP * Qp + i;
-
-      R fr[NP];
-  #pragma unroll
-      for (int m = 0; m < NP; ++m) fr[m] = decode<ST>(frow[m * Qp], w, ws);
-
-      R flux[NF];
-  #pragma unroll
-      for (int fc = 0; fc < 3; ++fc) {
-        const R en = ex * g[4 + 3 * fc] + ey * g[5 + 3 * fc];
-        const R c = R(0.5) * (en - ab * fabs(en)) * g[6 + 3 * fc];
-        const int code = sm.nbr[e * 3 + fc];
-        if (code >= 0) {
-          R wsn = 0;
-          if constexpr (ST::dev) wsn = w * sm.nscale[e * 3 + fc];
-          const S* trow = sm.tr + size_t(e * NF + fc * NFP) * Qp + i;
-  #pragma unroll
-          for (int aa = 0; aa < NFP; ++aa)
-            flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - decode<ST>(trow[aa * Qp], w, wsn));
-        } else if (en < R(0)) {
-          const int slot = -code - 1;  // wall slot: 4 * case + side
-          const R fb = __ldg(a.wall_feq + slot * Qp + i);
-          const R den_inv = __ldg(a.wall_den_inv + slot);
-          const bool diffuse = den_inv > R(0);
-          const R scale = diffuse ? den_inv * fb : R(0);
-  #pragma unroll
-          for (int aa = 0; aa < NFP; ++aa) {
-            const R fp = diffuse ? sm.wn[e * NF + fc * NFP + aa] * scale : fb;
-            flux[fc * NFP + aa] = c * (fr[face_node(fc, aa)] - fp);
-          }
-        } else {
-  #pragma unroll
-          for (int aa = 0; aa < NFP; ++aa) flux[fc * NFP + aa] = R(0);
-        }
-      }
-
-      float dloc = 0.f;
-      R invw = 0;
-      if constexpr (ST::dev) invw = __ldg(a.vel + kVelInvW * Qp + i);
-  #pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        R dr = 0, ds = 0;
-  #pragma unroll
-        for (int m = 0; m < NP; ++m) {
-          dr = fma(opv<R>(OFF_DR + n * NP + m), fr[m], dr);
-          ds = fma(opv<R>(OFF_DS + n * NP + m), fr[m], ds);
-        }
-        R lf = 0;
-  #pragma unroll
-        for (int j = 0; j < NF; ++j) lf = fma(opv<R>(OFF_LIFT + n * NF + j), flux[j], lf);
-        R rhs = fma(-ar, dr, fma(-as, ds, lf));
-        rhs += collision<R>(sm.mom + (size_t(e) * NP + n) * 8, ex, ey, w, fr[n], inv_tau, third);
-        R r = dt * rhs;
-        if (read_res) r = fma(rkA, rrow[n * Qp], r);
-        rrow[n * Qp] = r;
-        const R fnew = new_f<ST>(fr[n], rkB, r);
-        if constexpr (ST::dev) {
-          dloc = fmaxf(dloc, fabsf((fnew - w) * invw));
-        } else {
-          frow[n * Qp] = S(fnew);
-        }
-      }
-      if constexpr (ST::dev) {
-        if (e != emax) {
-          if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
-          emax = e;
-          dmax = 0.f;
-        }
-        dmax = fmaxf(dmax, dloc);
-      }
-    }
-
-    }
+    item_update<ST, QT, items_vpt<ST, QT>()>(a, sm, k0, ne, read_res, dmax, emax);
 
     // ---- 5. deviation forms: new per-element scale, encoding in place ------------
     if constexpr (ST::dev) {
