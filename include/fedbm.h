@@ -109,6 +109,10 @@ typedef struct fedbm_params {
                             <= 256 (0 = auto)                                  */
   int32_t pipeline_stages; /* stage-kernel tile buffers per CTA: 1, or 2 to load
                               the next tile while computing one (0 = auto = 1) */
+  int32_t test_wait_timeout; /* test hook, keep 0: when 1, every stage kernel
+                              waits for 16 bytes that never arrive, so its
+                              bounded wait (about 3 s) runs out, the kernel
+                              returns and fedbm_mass reports FEDBM_ETIMEOUT  */
 } fedbm_params;
 
 typedef struct fedbm_info_t {

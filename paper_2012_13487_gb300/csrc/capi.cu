@@ -281,6 +281,7 @@ struct Group {
   fedbm_velset_desc vd{};
   int collision = 1, reduction = 0;
   double beta = 1.0;
+  int test_wait_timeout = 0;
   int64_t K = 0;
   std::vector<int> cases;
   int epc = 0, tpb = 0, nstages = 1, grid = 0;
@@ -325,7 +326,8 @@ bool same_group(const Group& g, const fedbm_mesh_desc& md, const fedbm_velset_de
   return g.p == md.order && g.store == prm.precision && g.vd.kind == vd.kind && g.vd.n == vd.n &&
          g.vd.nc_extent == vd.nc_extent && g.vd.nc_sqrt2 == vd.nc_sqrt2 && g.vd.eq_order == vd.eq_order &&
          g.collision == prm.collision && g.reduction == prm.reduction && g.beta == prm.beta &&
-         g.epc == prm.elems_per_cta && g.tpb == prm.threads_per_cta && g.nstages == prm.pipeline_stages;
+         g.epc == prm.elems_per_cta && g.tpb == prm.threads_per_cta && g.nstages == prm.pipeline_stages &&
+         g.test_wait_timeout == prm.test_wait_timeout;
 }
 
 template <typename R>
@@ -355,6 +357,7 @@ void fill_stage_args(const Group& g, int stage, int from, StageArgs<R>& a) {
   a.eq_order = g.vd.eq_order;
   a.red = g.reduction;
   a.err = g.flag + 1;
+  a.extra_tx = g.test_wait_timeout ? 16u : 0u;
 }
 
 cudaError_t launch_stage(const Group& g, int stage, int from, cudaStream_t st) {
@@ -731,6 +734,7 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
       g.epc = prm.elems_per_cta;
       g.tpb = prm.threads_per_cta;
       g.nstages = prm.pipeline_stages;
+      g.test_wait_timeout = prm.test_wait_timeout;
       b->groups.push_back(g);
       gi = int(b->groups.size()) - 1;
     }

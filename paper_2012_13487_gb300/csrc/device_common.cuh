@@ -77,6 +77,7 @@ struct StageArgs {
   R rkA, rkB, ab;
   int32_t collision, eq_order, red;
   int* err;                 // set to 1 if a bounded wait of a CTA gave up
+  uint32_t extra_tx;        // test hook: bytes expected on top of the copies (0)
 };
 
 __host__ __device__ constexpr int np_of(int p) { return (p + 1) * (p + 2) / 2; }

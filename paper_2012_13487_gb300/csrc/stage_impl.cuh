@@ -511,7 +511,7 @@ __device__ void issue_tile_loads(const StageArgs<typename ST::R>& a, StageSmem<t
     }
   }
   uint32_t bytes = 0;
-  if (lane == 0) bytes += tile_bytes + geo_bytes + (read_res ? res_bytes : 0u);
+  if (lane == 0) bytes += tile_bytes + geo_bytes + (read_res ? res_bytes : 0u) + a.extra_tx;
   for (int row = lane; row < ne * NF; row += 32) {
     const int code = __ldg(a.nbr + (k0 + row / NF) * 3 + (row % NF) / NFP);
     if (code >= 0) bytes += uint32_t(row_bytes);

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("reduction", ctypes.c_int32), ("collision", ctypes.c_int32),
                 ("elems_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("pipeline_stages", ctypes.c_int32)]
+                ("pipeline_stages", ctypes.c_int32), ("test_wait_timeout", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -165,12 +165,13 @@ def velset_desc(kind=VELSET_GH, n=4, eq_order=2, nc_extent=4.0, nc_sqrt2=0):
 
 
 def params(kn=1.0, precision=FP32, reduction=RED_DEFAULT, cfl=0.5, dt=0.0, beta=1.0, collision=1,
-           length=1.0, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0):
+           length=1.0, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0, test_wait_timeout=0):
     p = Params()
     p.kn, p.length, p.beta, p.cfl, p.dt = kn, length, beta, cfl, dt
     p.precision, p.reduction, p.collision = precision, reduction, collision
     p.elems_per_cta, p.threads_per_cta = elems_per_cta, threads_per_cta
     p.pipeline_stages = pipeline_stages
+    p.test_wait_timeout = test_wait_timeout
     return p
 
 

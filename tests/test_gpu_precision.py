@@ -1,0 +1,72 @@
+"""Storage-precision error report on the 32x32x2 copy of the rarefied cavity
+(Kn = 8, p = 3, NC 32x32 velocities, lid speed 0.1): one LSRK(5,4) step from a
+perturbed rest state in every reduced storage form, against the FP64 oracle.
+
+Bound for the 16-bit deviation forms (f = w (1 + s q), s a power of two per
+element with |q| < 2^qmax): one encoding changes f by at most w md u, md the
+element's largest |f/w - 1| and u = 2^-8 for BF16 (8 significant bits, q in
+(-1, 1)) or 2^-11 for FP16 (11 significant bits, |q| < 2^15).  One step
+encodes six times (the initial state and the five stage outputs); the stage
+operator may amplify an input error by O(1), so the test allows 12 u.  The
+FP32 form is held to the per-stage rounding bound of the parity tests.
+"""
+import numpy as np
+import pytest
+
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+CASE = cases.cavity(32, 32, 3, velset=("nc", 32), kn=8.0, U=0.1)
+
+
+@pytest.fixture(scope="module")
+def oracle_step():
+    pr = cases.oracle_problem(CASE)
+    f0 = cases.initial_state(pr, amp=1e-3, seed=83)
+    f1 = pr.run(f0, 1)
+    return pr, f0, f1
+
+
+def _gpu_step(f0, prec, red):
+    s = cases.solver(CASE, prec, red)
+    s.set_state(f0)
+    s.step(1)
+    f = s.state()
+    rho, ux, uy = s.moments()
+    s.mass()
+    s.close()
+    return f, rho, ux, uy
+
+
+def _report(pr, f, f1, rho, ux, uy):
+    w = pr.w[None, None, :]
+    md = np.abs(f1 / w - 1.0).max(axis=(1, 2))             # per element
+    norm_err = (np.abs(f - f1) / (w * md[:, None, None])).max()
+    orho, oux, ouy = pr.nodal_moments(f1)
+    zero = lambda x, y: 0 * x
+    e_rho = pr.l2_error(rho - orho, zero)
+    e_u = np.hypot(pr.l2_error(ux - oux, zero), pr.l2_error(uy - ouy, zero)) / 0.1
+    e_f = float(np.sqrt(((f - f1) ** 2).sum() / (f1 ** 2).sum()))
+    return float(norm_err), float(e_rho), float(e_u), e_f
+
+
+@pytest.mark.parametrize("prec,red,u", [("bf16", "fp64", 2.0 ** -8), ("bf16", "comp", 2.0 ** -8),
+                                        ("fp16", "fp64", 2.0 ** -11), ("fp16", "comp", 2.0 ** -11)])
+def test_deviation_storage_error_c3_copy(oracle_step, prec, red, u):
+    pr, f0, f1 = oracle_step
+    f, rho, ux, uy = _gpu_step(f0, prec, red)
+    norm_err, e_rho, e_u, e_f = _report(pr, f, f1, rho, ux, uy)
+    print(f"{prec}/{red}: max|df|/(w md) = {norm_err:.3e} (bound {12 * u:.3e}), "
+          f"L2 rho {e_rho:.3e}, L2 u/U {e_u:.3e}, rel L2 f {e_f:.3e}")
+    assert norm_err < 12 * u, norm_err
+    assert e_rho < 12 * u and e_u < 12 * u * 10, (e_rho, e_u)
+
+
+def test_fp32_state_error_c3_copy(oracle_step):
+    pr, f0, f1 = oracle_step
+    f, rho, ux, uy = _gpu_step(f0, "fp32", "default")
+    norm_err, e_rho, e_u, e_f = _report(pr, f, f1, rho, ux, uy)
+    print(f"fp32: rel max {cases.rel_max_err(f, f1):.3e}, L2 rho {e_rho:.3e}, L2 u/U {e_u:.3e}")
+    assert cases.rel_max_err(f, f1) < 4.0 * pr.Np * U32 * np.sqrt(5) + U32
