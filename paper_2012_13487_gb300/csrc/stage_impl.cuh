@@ -19,11 +19,28 @@
 //      as the coefficients of f^eq/tau per node;
 //   3. wall numerators sum_{e.n>0} (e.n) f^- of eq. FullBC per wall node;
 //   4. residual and update, one thread per (element, velocity) item, with
-//      Dr, Ds, LIFT as constant-memory operands of unrolled FMAs;
+//      Dr, Ds, LIFT as constant-memory operands of unrolled FMAs (the 16-bit
+//      forms up to degree 4 take two velocities per thread as packed FP32
+//      pairs, fma.rn.f32x2);
 //   5. deviation forms only: per-element scale from max |f/w - 1|, encode;
 //   6. bulk-store the new state and residual tiles.
 #include "device_common.cuh"
 #include "stage_dispatch.h"
+
+#include <cstring>
+
+// Largest degree whose 16-bit forms take two velocities per thread (and the
+// FP32 state too when FEDBM_VPT2_FP32_STATE is 1); FEDBM_PACKED_FMA = 1 runs
+// the two velocities' contractions as packed FP32 pairs.
+#ifndef FEDBM_VPT2_MAX_P
+#define FEDBM_VPT2_MAX_P 4
+#endif
+#ifndef FEDBM_VPT2_FP32_STATE
+#define FEDBM_VPT2_FP32_STATE 0
+#endif
+#ifndef FEDBM_PACKED_FMA
+#define FEDBM_PACKED_FMA 1
+#endif
 
 #ifndef FEDBM_P
 #error "FEDBM_P must be defined"
@@ -43,6 +60,8 @@ constexpr int OPS_N = 2 * NP * NP + NP * NF;
 
 static __constant__ float c_ops32[OPS_N];
 static __constant__ double c_ops64[OPS_N];
+// every FP32 coefficient twice, as the broadcast operand of a packed FMA
+static __constant__ unsigned long long c_ops32x2[OPS_N];
 
 template <typename R>
 __device__ __forceinline__ R opv(int idx);
@@ -58,6 +77,23 @@ __host__ __device__ constexpr int face_node(int f, int a) {
 }
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Packed FP32 pairs (two velocities of one node in a 64-bit register pair):
+// fma.rn.f32x2 rounds each half exactly like fmaf.
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long p, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 
 // ---- moment accumulators ----------------------------------------------------
 struct AccD {
@@ -322,7 +358,9 @@ __device__ __forceinline__ R collision(const R* mm, R ex, R ey, R w, R f, R inv_
 // feeds two FMAs and the per-item set-up is shared), else one.
 template <class ST, int QT>
 __host__ __device__ constexpr int items_vpt() {
-  return (QT > 0 && ST::dev && P <= 4) ? 2 : 1;
+  return (QT > 0 && sizeof(typename ST::R) == 4 && (ST::dev || FEDBM_VPT2_FP32_STATE) && P <= FEDBM_VPT2_MAX_P)
+             ? 2
+             : 1;
 }
 
 template <typename T, int N>
@@ -347,6 +385,7 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
   const int tid = threadIdx.x, nth = blockDim.x;
   const R rkA = a.rkA, rkB = a.rkB, ab = a.ab;
   const bool third = a.eq_order == 3;
+  constexpr bool kPacked = FEDBM_PACKED_FMA && sizeof(R) == 4 && VPT == 2;
   for (int item = tid; item < ne * Qv; item += nth) {
     const int e = item / Qv;
     const int i = (item - e * Qv) * VPT;
@@ -425,22 +464,38 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
       RV rold;
       if (read_res) rold = *reinterpret_cast<const RV*>(rrow + n * Qp);
       R dr[VPT], ds[VPT], lf[VPT];
+      if constexpr (kPacked) {
+        // two velocities per packed FMA; the same rounding as the scalar form
+        unsigned long long drp = 0ull, dsp = 0ull, lfp = 0ull;
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) dr[v] = ds[v] = lf[v] = R(0);
-#pragma unroll
-      for (int m = 0; m < NP; ++m) {
-        const R cr = opv<R>(OFF_DR + n * NP + m), cs = opv<R>(OFF_DS + n * NP + m);
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          dr[v] = fma(cr, fr[v][m], dr[v]);
-          ds[v] = fma(cs, fr[v][m], ds[v]);
+        for (int m = 0; m < NP; ++m) {
+          const unsigned long long x = f2pack(fr[0][m], fr[1][m]);
+          drp = f2fma(c_ops32x2[OFF_DR + n * NP + m], x, drp);
+          dsp = f2fma(c_ops32x2[OFF_DS + n * NP + m], x, dsp);
         }
-      }
 #pragma unroll
-      for (int j = 0; j < NF; ++j) {
-        const R cl = opv<R>(OFF_LIFT + n * NF + j);
+        for (int j = 0; j < NF; ++j) lfp = f2fma(c_ops32x2[OFF_LIFT + n * NF + j], f2pack(flux[0][j], flux[1][j]), lfp);
+        f2unpack(drp, dr[0], dr[VPT - 1]);
+        f2unpack(dsp, ds[0], ds[VPT - 1]);
+        f2unpack(lfp, lf[0], lf[VPT - 1]);
+      } else {
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) lf[v] = fma(cl, flux[v][j], lf[v]);
+        for (int v = 0; v < VPT; ++v) dr[v] = ds[v] = lf[v] = R(0);
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const R cr = opv<R>(OFF_DR + n * NP + m), cs = opv<R>(OFF_DS + n * NP + m);
+#pragma unroll
+          for (int v = 0; v < VPT; ++v) {
+            dr[v] = fma(cr, fr[v][m], dr[v]);
+            ds[v] = fma(cs, fr[v][m], ds[v]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+          const R cl = opv<R>(OFF_LIFT + n * NF + j);
+#pragma unroll
+          for (int v = 0; v < VPT; ++v) lf[v] = fma(cl, flux[v][j], lf[v]);
+        }
       }
       const R* mm = sm.mom + (size_t(e) * NP + n) * 8;
       RV rr;
@@ -755,8 +810,16 @@ cudaError_t upload(const double* Dr, const double* Ds, const double* LIFT) {
     h64[OFF_DS + j] = Ds[j];
   }
   for (int j = 0; j < NP * NF; ++j) h64[OFF_LIFT + j] = LIFT[j];
-  for (int j = 0; j < OPS_N; ++j) h32[j] = float(h64[j]);
+  unsigned long long h32x2[OPS_N];
+  for (int j = 0; j < OPS_N; ++j) {
+    h32[j] = float(h64[j]);
+    uint32_t bits;
+    std::memcpy(&bits, &h32[j], 4);
+    h32x2[j] = (static_cast<unsigned long long>(bits) << 32) | bits;
+  }
   cudaError_t e = cudaMemcpyToSymbol(c_ops64, h64, sizeof(h64));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_ops32x2, h32x2, sizeof(h32x2));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_ops32, h32, sizeof(h32));
 }
