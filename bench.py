@@ -90,7 +90,7 @@ def dims(w):
 
 def stage_kernel_sha():
     h = hashlib.sha256()
-    for n in ("stage_impl.cuh", "device_common.cuh"):
+    for n in ("stage_impl.cuh", "stage_tc.cuh", "device_common.cuh"):
         with open(os.path.join(ROOT, "paper_2012_13487_gb300", "csrc", n), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -172,7 +172,7 @@ class ClockSampler:
                                                     if r[3].replace(".", "").isdigit()) if rows else None}
 
 
-def make_descriptors(w, epc=0, tpb=0, stages=0):
+def make_descriptors(w, epc=0, tpb=0, stages=0, tc=0):
     from paper_2012_13487_gb300 import fedbm as fb
     if w["kind"] == "cavity":
         bc = (fb.BC_WALL_DIFFUSE,) * 4
@@ -184,13 +184,13 @@ def make_descriptors(w, epc=0, tpb=0, stages=0):
     kind, n = w["vel"]
     v = fb.velset_desc(fb.VELSET_GH if kind == "gh" else fb.VELSET_NC, n, eq_order=w.get("eq_order", 2))
     prm = fb.params(kn=w["kn"], precision=PREC[w["precision"]], reduction=RED[w.get("reduction", "default")],
-                    cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb, pipeline_stages=stages)
+                    cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb, pipeline_stages=stages, tensor_cores=tc)
     return m, v, prm
 
 
-def make_solver(w, stream_handle, epc=0, tpb=0, stages=0):
+def make_solver(w, stream_handle, epc=0, tpb=0, stages=0, tc=0):
     from paper_2012_13487_gb300 import fedbm as fb
-    return fb.Solver(*make_descriptors(w, epc, tpb, stages), stream_handle)
+    return fb.Solver(*make_descriptors(w, epc, tpb, stages, tc), stream_handle)
 
 
 def make_batch(cases, stream_handle):
@@ -337,9 +337,9 @@ def run_ours(args, w, name):
         return run_batch_workload(args, w, name, st, world, rank, dist)
     K, Np, Q = dims(w)
     dof = K * Np * Q
-    s = make_solver(w, st.cuda_stream, args.epc, args.tpb, args.stages)
+    s = make_solver(w, st.cuda_stream, args.epc, args.tpb, args.stages, args.tc)
     s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
-    if not args.no_tune and not (args.epc or args.tpb or args.stages):
+    if not args.no_tune and not (args.epc or args.tpb or args.stages or args.tc == 1):
         s.autotune(None, 5)
     s.step(args.warmup)
     torch.cuda.synchronize()
@@ -437,7 +437,8 @@ def run_ours(args, w, name):
             "data": "synthetic",
             "config": {"workload": w["desc"], "name": name, "K": K, "Np": Np, "Q": Q, "dof": dof,
                        "tile": {"elems_per_cta": s.info.elems_per_cta, "threads_per_cta": s.info.threads_per_cta,
-                                "pipeline_stages": s.info.pipeline_stages, "grid": s.info.grid},
+                                "pipeline_stages": s.info.pipeline_stages, "grid": s.info.grid,
+                                "tensor_cores": s.info.tensor_cores},
                        "l2": "inputs larger than L2 (state x2 + residual = %.0f MB), no flush" %
                              (dof * (2 * STATE_BYTES[w["precision"]] + RES_BYTES[w["precision"]]) / 1e6),
                        "parallelism": "replicas x%d" % world},
@@ -445,7 +446,8 @@ def run_ours(args, w, name):
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": traffic,
                          "algorithmic_bytes_per_dof_step": algorithmic_bytes_per_dof_step(w["precision"]),
-                         "kernel": "stage_kernel (5 launches per step; average over the mix)"},
+                         "kernel": ("stage_kernel_tc" if s.info.tensor_cores else "stage_kernel")
+                                   + " (5 launches per step; average over the mix)"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "DOF-stage/s", "steps": e2e_steps,
                     "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": 3 * K * Np * 8,
@@ -508,7 +510,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -516,6 +518,8 @@ def main():
     ap.add_argument("--epc", type=int, default=0, help="stage tile: elements per CTA (0 = library default)")
     ap.add_argument("--tpb", type=int, default=0, help="stage tile: threads per CTA (0 = library default)")
     ap.add_argument("--stages", type=int, default=0, help="stage tile buffers per CTA (0 = library default)")
+    ap.add_argument("--tc", type=int, default=0, choices=[-1, 0, 1],
+                    help="stage-kernel form: 1 tensor cores, -1 FMA only, 0 library default")
     ap.add_argument("--no-tune", action="store_true", help="skip the tile autotuner")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched form measurements")
     args = ap.parse_args()

@@ -109,6 +109,13 @@ typedef struct fedbm_params {
                             <= 256 (0 = auto)                                  */
   int32_t pipeline_stages; /* stage-kernel tile buffers per CTA: 1, or 2 to load
                               the next tile while computing one (0 = auto = 1) */
+  int32_t tensor_cores;  /* stage-kernel form: 0 = tensor cores (tcgen05 TF32
+                            MMAs for the Dr, Ds, LIFT contractions) where the
+                            form has them and no tile is given above, else the
+                            FMA kernel; 1 = tensor cores required (EINVAL where
+                            the form has none); -1 = FMA kernel only.  The
+                            tensor-core form exists for FP32 state with 128 or
+                            256 padded velocities and degree <= 4           */
   int32_t test_wait_timeout; /* test hook, keep 0: when 1, every stage kernel
                               waits for 16 bytes that never arrive, so its
                               bounded wait (about 3 s) runs out, the kernel
@@ -123,6 +130,8 @@ typedef struct fedbm_info_t {
   int32_t elems_per_cta, threads_per_cta;
   int32_t pipeline_stages, grid; /* stage-kernel buffers per CTA; persistent grid */
   int32_t group, ngroups;        /* batches: kernel group of this case; group count */
+  int32_t tensor_cores;          /* 1 if the group's stage kernel is the tensor-core form */
+  int32_t reserved0;
   int64_t state_bytes;           /* device bytes of one state buffer             */
   int64_t residual_bytes;        /* device bytes of the RK residual              */
 } fedbm_info_t;
@@ -241,14 +250,20 @@ int fedbm_batch_mass(fedbm_batch* b, int32_t c, double* total_mass);
 int fedbm_batch_info(const fedbm_batch* b, int32_t c, fedbm_info_t* info);
 /* Advance every case nsteps LSRK(5,4) steps (one graph launch per step). */
 int fedbm_batch_rk_step(fedbm_batch* b, int32_t nsteps);
-/* Re-tile one group's stage kernel (0 = automatic for each argument); used by
- * the tile autotuner.  Takes effect from the next step. */
+/* Re-tile one group's stage kernel as the FMA form (0 = automatic for each
+ * argument); used by the tile autotuner.  Takes effect from the next step. */
 int fedbm_batch_set_tiles(fedbm_batch* b, int32_t group, int32_t elems_per_cta,
                           int32_t threads_per_cta, int32_t pipeline_stages);
+/* Switch one group's stage kernel to the tensor-core form (on = 1; EINVAL if
+ * the group's form has none, or if it was created with tensor_cores = -1) or
+ * back to the FMA form with automatic tiles (on = 0).  Next step onwards. */
+int fedbm_batch_set_tensor_cores(fedbm_batch* b, int32_t group, int32_t on);
 
 /* Tile autotuner: for every kernel group, time each candidate stage-kernel
  * tile (elements per CTA 1..32, threads per CTA 64/128/256, one or two
- * pipeline stages) on `trials` launches (0 means 5) and keep the fastest.
+ * pipeline stages, and the tensor-core form where the group has it and was
+ * not created with tensor_cores = -1) on `trials` launches (0 means 5) and
+ * keep the fastest.
  * The current state is left unchanged.  With a cache_path (NULL or "" for
  * none), results are read from and written to a JSON object keyed by device
  * name, degree, padded velocity count, precision, reduction and element

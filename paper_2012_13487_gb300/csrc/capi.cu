@@ -282,6 +282,8 @@ struct Group {
   int collision = 1, reduction = 0;
   double beta = 1.0;
   int test_wait_timeout = 0;
+  int tc_mode = 0;  // fedbm_params.tensor_cores of the group's cases
+  int tc = 0;       // 1: the stage kernel is the tensor-core form
   int64_t K = 0;
   std::vector<int> cases;
   int epc = 0, tpb = 0, nstages = 1, grid = 0;
@@ -327,7 +329,7 @@ bool same_group(const Group& g, const fedbm_mesh_desc& md, const fedbm_velset_de
          g.vd.nc_extent == vd.nc_extent && g.vd.nc_sqrt2 == vd.nc_sqrt2 && g.vd.eq_order == vd.eq_order &&
          g.collision == prm.collision && g.reduction == prm.reduction && g.beta == prm.beta &&
          g.epc == prm.elems_per_cta && g.tpb == prm.threads_per_cta && g.nstages == prm.pipeline_stages &&
-         g.test_wait_timeout == prm.test_wait_timeout;
+         g.test_wait_timeout == prm.test_wait_timeout && g.tc_mode == prm.tensor_cores;
 }
 
 template <typename R>
@@ -369,11 +371,54 @@ cudaError_t launch_stage(const Group& g, int stage, int from, cudaStream_t st) {
   }
   StageArgs<float> a;
   fill_stage_args(g, stage, from, a);
+  if (g.tc) return e.launch_tc(&a, g.grid, g.smem, st);
   return e.launch(g.store, &a, g.grid, g.tpb, g.smem, st);
 }
 
+void drop_graphs(Batch& b) {
+  for (int c = 0; c < 2; ++c)
+    if (b.graph[c]) {
+      cudaGraphExecDestroy(b.graph[c]);
+      b.graph[c] = nullptr;
+    }
+}
+
+// The tensor-core form of a group: one element per CTA, one thread per
+// velocity.  Each CTA holds tc_tmem_cols tensor-memory columns for its whole
+// life; the resident CTAs of an SM must fit in its 512 columns so that an
+// allocation never waits on another CTA of the same kernel.
+int configure_tc(Batch& b, Group& g) {
+  const StageEntry e = stage_entry(g.p);
+  size_t smem = e.tc_smem(g.store, g.Qp);
+  if (g.tc_mode < 0 || smem == 0) return fail(FEDBM_EINVAL, "this form has no tensor-core stage kernel");
+  int nsm = 0;
+  FEDBM_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device));
+  int smem_sm = 0;
+  FEDBM_CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b.device));
+  // small tiles: reserve enough shared memory that no more CTAs fit on an SM
+  // than its tensor memory serves
+  const int max_ctas = 512 / e.tc_tmem_cols(g.Qp);
+  smem = std::max(smem, size_t(smem_sm) / size_t(max_ctas + 1) + 1024);
+  FEDBM_CK(e.set_smem_tc(g.Qp, smem));
+  const int per_sm = e.occupancy_tc(g.Qp, smem);
+  const int by_smem = int(size_t(smem_sm) / smem);
+  if (per_sm < 1 || std::max(per_sm, by_smem) * e.tc_tmem_cols(g.Qp) > 512)
+    return fail(FEDBM_EINVAL, "tensor-core stage kernel cannot be resident within tensor memory");
+  g.tc = 1;
+  g.epc = 1;
+  g.tpb = g.Qp;
+  g.nstages = 1;
+  g.smem = smem;
+  g.grid = int(std::min<int64_t>(g.K, int64_t(per_sm) * nsm));
+  drop_graphs(b);
+  return FEDBM_OK;
+}
+
+bool tc_available(const Group& g) { return g.tc_mode >= 0 && stage_entry(g.p).tc_smem(g.store, g.Qp) > 0; }
+
 // Tile shape, pipeline depth and persistent grid of a group's stage kernel.
 int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
+  g.tc = 0;
   g.epc = epc > 0 ? epc : (g.Qp < 128 ? std::max(1, 128 / g.Qp) : 1);
   g.tpb = tpb > 0 ? tpb : std::min(128, std::max(32, (g.epc * g.Qp + 31) / 32 * 32));
   if (g.tpb % 32 || g.tpb > 256) return fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256");
@@ -393,11 +438,7 @@ int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
   if (per_sm < 1) return fail(FEDBM_EINVAL, "stage tile cannot be resident on an SM");
   const int64_t ntiles = (g.K + g.epc - 1) / g.epc;
   g.grid = int(std::min<int64_t>(ntiles, int64_t(per_sm) * nsm));
-  for (int c = 0; c < 2; ++c)
-    if (b.graph[c]) {
-      cudaGraphExecDestroy(b.graph[c]);
-      b.graph[c] = nullptr;
-    }
+  drop_graphs(b);
   return FEDBM_OK;
 }
 
@@ -410,9 +451,13 @@ int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
 // Results are cached per (device, degree, velocity count, precision,
 // element count) in a flat JSON object, one entry per line.
 struct TuneEntry {
-  int epc = 0, tpb = 0, stages = 0;
+  int epc = 0, tpb = 0, stages = 0, tc = 0;
   double us = 0;
 };
+
+int apply_tune(Batch& b, Group& g, const TuneEntry& t) {
+  return t.tc ? configure_tc(b, g) : configure_tiles(b, g, t.epc, t.tpb, t.stages);
+}
 
 std::string tune_key(const Batch& b, const Group& g) {
   cudaDeviceProp prop;
@@ -432,8 +477,8 @@ std::vector<std::pair<std::string, TuneEntry>> read_tune_cache(const char* path)
   while (std::fgets(line, sizeof(line), fp)) {
     char key[512];
     TuneEntry t;
-    if (std::sscanf(line, " \"%511[^\"]\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"us\": %lf}", key, &t.epc,
-                    &t.tpb, &t.stages, &t.us) == 5)
+    if (std::sscanf(line, " \"%511[^\"]\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"tc\": %d, \"us\": %lf}", key,
+                    &t.epc, &t.tpb, &t.stages, &t.tc, &t.us) == 6)
       out.emplace_back(key, t);
   }
   std::fclose(fp);
@@ -446,9 +491,9 @@ void write_tune_cache(const char* path, const std::vector<std::pair<std::string,
   if (!fp) return;
   std::fprintf(fp, "{\n");
   for (size_t j = 0; j < entries.size(); ++j)
-    std::fprintf(fp, "\"%s\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"us\": %.3f}%s\n",
+    std::fprintf(fp, "\"%s\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"tc\": %d, \"us\": %.3f}%s\n",
                  entries[j].first.c_str(), entries[j].second.epc, entries[j].second.tpb, entries[j].second.stages,
-                 entries[j].second.us, j + 1 < entries.size() ? "," : "");
+                 entries[j].second.tc, entries[j].second.us, j + 1 < entries.size() ? "," : "");
   std::fprintf(fp, "}\n");
   std::fclose(fp);
 }
@@ -462,16 +507,31 @@ int autotune(Batch& b, const char* cache_path, int trials) {
   FEDBM_CK(cudaEventCreate(&e1));
   int rc = FEDBM_OK;
   for (Group& g : b.groups) {
+    if (g.tc_mode > 0) {  // tensor cores required: nothing to choose
+      if ((rc = configure_tc(b, g)) != FEDBM_OK) break;
+      continue;
+    }
     const std::string key = tune_key(b, g);
     const TuneEntry* hit = nullptr;
     for (auto& kv : cache)
       if (kv.first == key) hit = &kv.second;
-    if (hit) {
-      if ((rc = configure_tiles(b, g, hit->epc, hit->tpb, hit->stages)) != FEDBM_OK) break;
+    if (hit && (!hit->tc || tc_available(g))) {
+      if ((rc = apply_tune(b, g, *hit)) != FEDBM_OK) break;
       continue;
     }
     TuneEntry best;
     best.us = 1e300;
+    auto time_current = [&](TuneEntry cand) {
+      if (launch_stage(g, 1, b.cur, b.stream) != cudaSuccess) return;  // warm-up
+      cudaEventRecord(e0, b.stream);
+      for (int t = 0; t < trials; ++t) launch_stage(g, 1, b.cur, b.stream);
+      cudaEventRecord(e1, b.stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cand.us = 1e3 * double(ms) / trials;
+      if (cand.us < best.us) best = cand;
+    };
     const int epcs[] = {1, 2, 4, 8, 16, 32};
     const int tpbs[] = {64, 128, 256};
     for (int epc : epcs) {
@@ -480,29 +540,28 @@ int autotune(Batch& b, const char* cache_path, int trials) {
         if (tpb > 32 * ((epc * g.Qp + 31) / 32) * 2) continue;  // at most half the threads idle
         for (int stages = 1; stages <= 2; ++stages) {
           if (configure_tiles(b, g, epc, tpb, stages) != FEDBM_OK || g.nstages != stages) continue;
-          if (launch_stage(g, 1, b.cur, b.stream) != cudaSuccess) continue;  // warm-up
-          cudaEventRecord(e0, b.stream);
-          for (int t = 0; t < trials; ++t) launch_stage(g, 1, b.cur, b.stream);
-          cudaEventRecord(e1, b.stream);
-          if (cudaEventSynchronize(e1) != cudaSuccess) continue;
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          const double us = 1e3 * double(ms) / trials;
-          if (us < best.us) {
-            best.epc = epc;
-            best.tpb = tpb;
-            best.stages = stages;
-            best.us = us;
-          }
+          TuneEntry cand;
+          cand.epc = epc;
+          cand.tpb = tpb;
+          cand.stages = stages;
+          time_current(cand);
         }
       }
+    }
+    if (tc_available(g) && configure_tc(b, g) == FEDBM_OK) {
+      TuneEntry cand;
+      cand.epc = 1;
+      cand.tpb = g.Qp;
+      cand.stages = 1;
+      cand.tc = 1;
+      time_current(cand);
     }
     cudaGetLastError();
     if (best.epc == 0) {
       rc = fail(FEDBM_ECUDA, "autotune: no tile candidate could run");
       break;
     }
-    if ((rc = configure_tiles(b, g, best.epc, best.tpb, best.stages)) != FEDBM_OK) break;
+    if ((rc = apply_tune(b, g, best)) != FEDBM_OK) break;
     cache.emplace_back(key, best);
     dirty = true;
   }
@@ -713,6 +772,7 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
     if (prm.reduction < FEDBM_RED_DEFAULT || prm.reduction > FEDBM_RED_COMP_FP32)
       return bail(fail(FEDBM_EINVAL, "unknown reduction mode"));
     if (!(prm.kn > 0)) return bail(fail(FEDBM_EINVAL, "kn must be > 0"));
+    if (prm.tensor_cores < -1 || prm.tensor_cores > 1) return bail(fail(FEDBM_EINVAL, "tensor_cores must be -1, 0 or 1"));
     if (!(prm.beta >= 0.5 && prm.beta <= 1.0)) return bail(fail(FEDBM_EINVAL, "beta must be in [0.5, 1]"));
     if (!(prm.dt > 0) && !(prm.cfl > 0)) return bail(fail(FEDBM_EINVAL, "need dt > 0 or cfl > 0"));
     if (cd[c].mesh.order < 0 || cd[c].mesh.order > kMaxOrder) return bail(fail(FEDBM_EINVAL, "order must be in 0..6"));
@@ -735,6 +795,7 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
       g.tpb = prm.threads_per_cta;
       g.nstages = prm.pipeline_stages;
       g.test_wait_timeout = prm.test_wait_timeout;
+      g.tc_mode = prm.tensor_cores;
       b->groups.push_back(g);
       gi = int(b->groups.size()) - 1;
     }
@@ -751,7 +812,12 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
          for (Group& g : b->groups) {
            const int epc = g.epc, tpb = g.tpb, st = g.nstages;
            if ((r = build_group(*b, g)) != FEDBM_OK) return r;
-           if ((r = configure_tiles(*b, g, epc, tpb, st)) != FEDBM_OK) return r;
+           const bool want_tc = g.tc_mode > 0 || (g.tc_mode == 0 && epc == 0 && tpb == 0 && st == 0 && tc_available(g));
+           if (want_tc) {
+             if ((r = configure_tc(*b, g)) != FEDBM_OK) return r;
+           } else if ((r = configure_tiles(*b, g, epc, tpb, st)) != FEDBM_OK) {
+             return r;
+           }
          }
          return FEDBM_OK;
        }()) != FEDBM_OK)
@@ -999,6 +1065,8 @@ int info(const Batch& b, int c, fedbm_info_t* out) {
   out->grid = g.grid;
   out->group = cs.group;
   out->ngroups = int32_t(b.groups.size());
+  out->tensor_cores = g.tc;
+  out->reserved0 = 0;
   out->state_bytes = cs.K * g.Np * g.Qp * int64_t(store_bytes(g.store));
   out->residual_bytes = cs.K * g.Np * g.Qp * int64_t(real_bytes(g.store));
   return FEDBM_OK;
@@ -1237,6 +1305,12 @@ extern "C" int fedbm_batch_set_tiles(fedbm_batch* h, int32_t group, int32_t elem
   FEDBM_BATCH(h, 0);
   if (group < 0 || group >= int(B.groups.size())) return fail(FEDBM_EINVAL, "group index out of range");
   return configure_tiles(B, B.groups[group], elems_per_cta, threads_per_cta, pipeline_stages);
+}
+
+extern "C" int fedbm_batch_set_tensor_cores(fedbm_batch* h, int32_t group, int32_t on) {
+  FEDBM_BATCH(h, 0);
+  if (group < 0 || group >= int(B.groups.size())) return fail(FEDBM_EINVAL, "group index out of range");
+  return on ? configure_tc(B, B.groups[group]) : configure_tiles(B, B.groups[group], 0, 0, 0);
 }
 
 extern "C" int fedbm_batch_autotune(fedbm_batch* h, const char* cache_path, int32_t trials) {

@@ -724,6 +724,8 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
   if (tid == 0) bulk_wait_read();
 }
 
+#include "stage_tc.cuh"
+
 template <class ST, int QT>
 cudaError_t launch_one(const void* args, int grid, int block, size_t smem, cudaStream_t st) {
   const auto& a = *static_cast<const StageArgs<typename ST::R>*>(args);
@@ -832,6 +834,11 @@ StageEntry FEDBM_STAGE_ENTRY_NAME() {
   s.set_smem = &set_smem;
   s.upload = &upload;
   s.occupancy = &occupancy;
+  s.tc_smem = &tc_smem;
+  s.tc_tmem_cols = &tc_tmem_cols;
+  s.launch_tc = &launch_tc;
+  s.set_smem_tc = &set_smem_tc;
+  s.occupancy_tc = &occupancy_tc;
   return s;
 }
 

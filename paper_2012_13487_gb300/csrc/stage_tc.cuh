@@ -1,0 +1,413 @@
+// Tensor-core form of the stage kernel (FP32 state, QT = 128 or 256 velocities,
+// one velocity per thread).  Included by stage_impl.cuh inside its namespace:
+// it reuses the tile loads, node moments, wall numerators and collision term of
+// the FMA kernel and replaces the element-local contractions of phase 4,
+//   V = (f - f_0 1) Dr^T,  W = (f - f_0 1) Ds^T,  Lf = flux LIFT^T,
+// by tcgen05 MMAs (kind::tf32, M = 128 velocities per MMA, accumulators in
+// tensor memory).  Subtracting the first node's value f_0 changes nothing in
+// exact arithmetic (Dr 1 = Ds 1 = 0, the derivative of a constant) and keeps
+// the operands small.  Each FP32 operand x is split into x_hi = tf32(x) and
+// x_lo = tf32(x - x_hi) and every product is taken as
+// a_hi b_hi + a_lo b_hi + a_hi b_lo (three MMAs), which keeps the contraction
+// error near FP32 rounding of the operands.
+//
+// Operands live in shared memory K-major without swizzle: a row of K values is
+// split into 16-byte chunks of 4 values; the 8 rows x 16 bytes of one chunk
+// column form a contiguous 128-byte core matrix; core matrix (row group g,
+// chunk c) sits at byte (g * KC + c) * 128.  In the matrix descriptor the
+// leading-dimension offset (next chunk along K) is 128 bytes and the stride
+// offset (next 8-row group) is KC * 128 bytes.
+
+namespace tc {
+
+constexpr int KD = (NP + 7) / 8 * 8;      // K of the derivative MMAs (nodes)
+constexpr int ND = (NP + 15) / 16 * 16;   // N of one derivative operator (nodes)
+constexpr int KL = (NF + 7) / 8 * 8;      // K of the lift MMA (face nodes)
+constexpr int NL = ND;                    // N of the lift MMA
+constexpr int KCD = KD / 4, KCL = KL / 4; // 16-byte chunks per operand row
+constexpr int CPM = 2 * ND + NL;          // accumulator columns per 128-velocity tile
+
+// tensor-memory columns of one CTA: a power of two >= 32 covering every tile
+__host__ __device__ constexpr int ncols_for(int QT) {
+  return (QT / 128) * CPM <= 32 ? 32 : (QT / 128) * CPM <= 64 ? 64 : (QT / 128) * CPM <= 128 ? 128
+         : (QT / 128) * CPM <= 256 ? 256 : 512;
+}
+
+// float index of (row r, column k) in a K-major operand with KC chunks per row
+__host__ __device__ constexpr int kidx(int r, int k, int KC) {
+  return ((r >> 3) * KC + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+// Shared-memory layout (byte offsets) of one CTA.
+struct Layout {
+  size_t bar, f, res, trF, A, B, L, geo, nbr, mom, wn, end;
+};
+__host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline Layout layout(int QT) {
+  Layout o;
+  size_t b = 0;
+  o.bar = b;  b += 32;                                       // tile barrier, MMA barrier, TMEM address
+  b = al(b, 128);
+  o.f = b;    b += size_t(NP) * QT * 4;                       // element tile (new state written back)
+  o.res = b;  b += size_t(NP) * QT * 4;                       // residual tile
+  b = al(b, 1024);
+  const size_t tr_bytes = size_t(NF) * QT * 4, fl_bytes = 2 * size_t(QT) * KL * 4;
+  o.trF = b;  b += al(tr_bytes > fl_bytes ? tr_bytes : fl_bytes, 1024);  // traces, then flux hi|lo
+  o.A = b;    b += 2 * size_t(QT) * KD * 4;                   // (f - f_0) hi|lo
+  o.B = b;    b += 2 * size_t(2 * ND) * KD * 4;               // [Dr; Ds] hi|lo
+  o.L = b;    b += 2 * size_t(NL) * KL * 4;                   // LIFT hi|lo
+  o.geo = b;  b += al(kGeoStrideDev * 4, 16);
+  o.nbr = b;  b += 16;
+  o.mom = b;  b += al(size_t(NP) * 8 * 4, 16);
+  o.wn = b;   b += al(size_t(NF) * 4, 16);
+  o.end = b;
+  return o;
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo with hi, lo in TF32 (bit patterns)
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = uint64_t((saddr >> 4) & 0x3FFF);
+  d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
+  d |= uint64_t(1) << 46;  // descriptor version of tcgen05; no swizzle, base offset 0
+  return d;
+}
+// instruction descriptor: D F32, A and B TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// N accumulator columns from taddr on (N a multiple of 16, up to 32)
+template <int N>
+__device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[N]) {
+  static_assert(N % 16 == 0 && N <= 32, "row chunk");
+  float t[16];
+#pragma unroll
+  for (int c = 0; c < N / 16; ++c) {
+    tmem_ld16(taddr + 16 * c, t);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[16 * c + j] = t[j];
+  }
+}
+
+// Writes row r (KC chunks of 4 values) of a K-major hi|lo operand pair:
+// x[k] - shift for k < LEN, zero beyond.
+template <int KC, int LEN>
+__device__ __forceinline__ void put_row(float* hi, float* lo, int r, const float (&x)[LEN], float shift) {
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * c + q;
+      const float v = k < LEN ? x[k] - shift : 0.f;
+      split_tf32(v, h[q], l[q]);
+    }
+    const int o = kidx(r, 4 * c, KC);
+    *reinterpret_cast<uint4*>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+}  // namespace tc
+
+// Persistent tensor-core stage kernel: CTA b handles elements b, b + gridDim.x,
+// ...; QT threads, thread t owns velocity t of the element throughout.
+template <int QT>
+__global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageArgs<float> a) {
+  using ST = StoreF32;
+  using namespace tc;
+  static_assert(QT == 128 || QT == 256, "one velocity per thread, whole 128-velocity MMA tiles");
+  constexpr int NCOLS = ncols_for(QT);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const Layout o = layout(QT);
+  uint64_t* bar_tile = reinterpret_cast<uint64_t*>(smem + o.bar);
+  uint64_t* bar_mma = bar_tile + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + o.bar + 16);
+  float* sA = reinterpret_cast<float*>(smem + o.A);
+  float* sF = reinterpret_cast<float*>(smem + o.trF);
+  float* sB = reinterpret_cast<float*>(smem + o.B);
+  float* sL = reinterpret_cast<float*>(smem + o.L);
+  StageSmem<float, float> sm;
+  sm.bar = bar_tile;
+  sm.f = reinterpret_cast<float*>(smem + o.f);
+  sm.res = reinterpret_cast<float*>(smem + o.res);
+  sm.tr = sF;
+  sm.geo = reinterpret_cast<float*>(smem + o.geo);
+  sm.nbr = reinterpret_cast<int*>(smem + o.nbr);
+  sm.scale = nullptr;
+  sm.nscale = nullptr;
+  sm.dmax = nullptr;
+  sm.mom = reinterpret_cast<float*>(smem + o.mom);
+  sm.wn = reinterpret_cast<float*>(smem + o.wn);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const float rkA = a.rkA, rkB = a.rkB, ab = a.ab;
+  const bool read_res = rkA != 0.f;
+  const bool third = a.eq_order == 3;
+  const int64_t ntiles = a.K;  // one element per tile
+
+  if (tid == 0) {
+    mbar_init(bar_tile, 32);
+    mbar_init(bar_mma, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "n"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // B operands from the FP64 operators: [Dr; Ds] (rows n, then ND + n) and LIFT
+  for (int v = tid; v < 2 * ND * KD; v += QT) {
+    const int n = v / KD, m = v % KD;
+    const int nn = n < ND ? n : n - ND;
+    double x = 0.0;
+    if (nn < NP && m < NP) x = c_ops64[(n < ND ? OFF_DR : OFF_DS) + nn * NP + m];
+    const float h = __uint_as_float(tf32_rna(float(x)));
+    sB[kidx(n, m, KCD)] = h;
+    sB[2 * ND * KD + kidx(n, m, KCD)] = __uint_as_float(tf32_rna(float(x - double(h))));
+  }
+  for (int v = tid; v < NL * KL; v += QT) {
+    const int n = v / KL, j = v % KL;
+    const double x = (n < NP && j < NF) ? c_ops64[OFF_LIFT + n * NF + j] : 0.0;
+    const float h = __uint_as_float(tf32_rna(float(x)));
+    sL[kidx(n, j, KCL)] = h;
+    sL[NL * KL + kidx(n, j, KCL)] = __uint_as_float(tf32_rna(float(x - double(h))));
+  }
+  fence_proxy_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+
+  int64_t tile = blockIdx.x;
+  if (tid < 32 && tile < ntiles) issue_tile_loads<ST, QT>(a, sm, tile, 1, read_res);
+
+  const float* vel = a.vel;
+  const float ex = __ldg(vel + kVelEx * QT + tid), ey = __ldg(vel + kVelEy * QT + tid);
+  const float w = __ldg(vel + kVelW * QT + tid);
+  const uint32_t sA_u = smem_u32(sA), sF_u = smem_u32(sF), sB_u = smem_u32(sB), sL_u = smem_u32(sL);
+
+  bool failed = false;
+  for (int j = 0; tile < ntiles; ++j, tile += gridDim.x) {
+    const int64_t k0 = tile;
+    if (j > 0 && tid < 32) {
+      if (tid == 0) bulk_wait_read();  // the previous tile's stores have read the buffers
+      __syncwarp();
+      issue_tile_loads<ST, QT>(a, sm, k0, 1, read_res);
+    }
+    const bool ok = mbar_wait_bounded(bar_tile, uint32_t(j & 1), 2000000000ull);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+
+    // ---- node moments and wall numerators (as in the FMA kernel) -----------------
+    if (!a.collision) {
+      for (int v = tid; v < NP * 8; v += QT) sm.mom[v] = 0.f;
+    } else if (a.red == kRedFP64) {
+      tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1);
+    } else if (a.red == kRedCompFP32) {
+      tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1);
+    } else {
+      tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1);
+    }
+    if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, 1);
+    __syncthreads();
+
+    // ---- this thread's velocity: state column, residual column, face fluxes -------
+    const int i = tid;
+    const float* g = sm.geo;
+    const float dt = g[kGeoDt], inv_tau = g[kGeoInvTau];
+    float fc[NP], rc[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+      fc[m] = sm.f[m * QT + i];
+      rc[m] = read_res ? sm.res[m * QT + i] : 0.f;
+    }
+    float flux[NF];
+#pragma unroll
+    for (int fcx = 0; fcx < 3; ++fcx) {
+      const float en = ex * g[4 + 3 * fcx] + ey * g[5 + 3 * fcx];
+      const float c = 0.5f * (en - ab * fabsf(en)) * g[6 + 3 * fcx];
+      const int code = sm.nbr[fcx];
+      if (code >= 0) {
+#pragma unroll
+        for (int aa = 0; aa < NFP; ++aa)
+          flux[fcx * NFP + aa] = c * (fc[face_node(fcx, aa)] - sm.tr[(fcx * NFP + aa) * QT + i]);
+      } else {
+        const int slot = -code - 1;  // wall slot: 4 * case + side
+        const float fb = __ldg(a.wall_feq + slot * QT + i);
+        const float den_inv = __ldg(a.wall_den_inv + slot);
+        const bool diffuse = den_inv > 0.f;
+        const float scale = diffuse ? den_inv * fb : 0.f;
+        // incoming velocities take the wall state; outgoing ones have no jump
+#pragma unroll
+        for (int aa = 0; aa < NFP; ++aa) {
+          const float fp = diffuse ? sm.wn[fcx * NFP + aa] * scale : fb;
+          flux[fcx * NFP + aa] = en < 0.f ? c * (fc[face_node(fcx, aa)] - fp) : 0.f;
+        }
+      }
+    }
+    __syncthreads();  // every trace has been read: the trace region takes the flux operand
+
+    // ---- operands, then the MMAs (one thread) --------------------------------------
+    put_row<KCD, NP>(sA, sA + QT * KD, i, fc, fc[0]);
+    put_row<KCL, NF>(sF, sF + QT * KL, i, flux, 0.f);
+    fence_proxy_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      constexpr uint32_t idD = idesc_tf32(128, 2 * ND), idL = idesc_tf32(128, NL);
+      constexpr uint32_t aHalfD = QT * KD * 4, aHalfL = QT * KL * 4;  // hi -> lo bytes
+      constexpr uint32_t bHalfD = 2 * ND * KD * 4, bHalfL = NL * KL * 4;
+#pragma unroll
+      for (int mt = 0; mt < QT / 128; ++mt) {
+        const uint32_t d = tmem + uint32_t(mt * CPM);
+        const uint32_t aoD = uint32_t(mt * 16 * KCD * 128), aoL = uint32_t(mt * 16 * KCL * 128);
+#pragma unroll
+        for (int ks = 0; ks < KD / 8; ++ks) {
+          const uint32_t ko = uint32_t(ks * 256);
+          const uint64_t ah = sdesc(sA_u + aoD + ko, 128, KCD * 128);
+          const uint64_t al = sdesc(sA_u + aHalfD + aoD + ko, 128, KCD * 128);
+          const uint64_t bh = sdesc(sB_u + ko, 128, KCD * 128), bl = sdesc(sB_u + bHalfD + ko, 128, KCD * 128);
+          mma_tf32(d, ah, bh, idD, ks > 0);
+          mma_tf32(d, al, bh, idD, 1);
+          mma_tf32(d, ah, bl, idD, 1);
+        }
+#pragma unroll
+        for (int ks = 0; ks < KL / 8; ++ks) {
+          const uint32_t ko = uint32_t(ks * 256);
+          const uint64_t ah = sdesc(sF_u + aoL + ko, 128, KCL * 128);
+          const uint64_t al = sdesc(sF_u + aHalfL + aoL + ko, 128, KCL * 128);
+          const uint64_t bh = sdesc(sL_u + ko, 128, KCL * 128), bl = sdesc(sL_u + bHalfL + ko, 128, KCL * 128);
+          mma_tf32(d + 2 * ND, ah, bh, idL, ks > 0);
+          mma_tf32(d + 2 * ND, al, bh, idL, 1);
+          mma_tf32(d + 2 * ND, ah, bl, idL, 1);
+        }
+      }
+      mma_commit(bar_mma);
+    }
+    const bool mok = mbar_wait_bounded(bar_mma, uint32_t(j & 1), 2000000000ull);
+    if (__syncthreads_or(!mok)) {
+      failed = true;
+      break;
+    }
+    fence_after_sync();
+
+    // ---- epilogue: rhs, collision, update --------------------------------------------
+    {
+      const uint32_t ta = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t((warp >> 2) * CPM);
+      float V[ND], W[ND], Lf[NL];
+      tmem_row<ND>(ta, V);
+      tmem_row<ND>(ta + ND, W);
+      tmem_row<NL>(ta + 2 * ND, Lf);
+      tmem_ld_wait();
+      const float ar = ex * g[0] + ey * g[2], as = ex * g[1] + ey * g[3];
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        float rhs = fmaf(-ar, V[n], fmaf(-as, W[n], Lf[n]));
+        rhs += collision<float>(sm.mom + n * 8, ex, ey, w, fc[n], inv_tau, third);
+        float r = dt * rhs;
+        if (read_res) r = fmaf(rkA, rc[n], r);
+        sm.res[n * QT + i] = r;
+        sm.f[n * QT + i] = fmaf(rkB, r, fc[n]);
+      }
+    }
+    fence_before_sync();
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      bulk_store(static_cast<float*>(a.f_out) + k0 * NP * QT, sm.f, uint32_t(NP * QT * 4));
+      bulk_store(a.res + k0 * NP * QT, sm.res, uint32_t(NP * QT * 4));
+      bulk_commit();
+    }
+  }
+  if (failed && tid == 0 && a.err) atomicExch(a.err, 1);
+  if (tid == 0) bulk_wait_read();
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(NCOLS));
+  }
+}
+
+// Largest degree with a tensor-core form.
+constexpr int kTcMaxP = 4;
+
+// Dynamic shared memory of the tensor-core kernel (0 = no tensor-core form).
+size_t tc_smem(int store_kind, int Qp) {
+  if (P > kTcMaxP || store_kind != kStoreF32 || (Qp != 128 && Qp != 256)) return 0;
+  return tc::layout(Qp).end;
+}
+
+// Tensor-memory columns one CTA of the tensor-core kernel allocates.
+int tc_tmem_cols(int Qp) { return tc::ncols_for(Qp); }
+
+cudaError_t launch_tc(const void* args, int grid, size_t smem, cudaStream_t st) {
+  if constexpr (P <= kTcMaxP) {
+    const auto& a = *static_cast<const StageArgs<float>*>(args);
+    if (a.Qp == 256) stage_kernel_tc<256><<<grid, 256, smem, st>>>(a);
+    else if (a.Qp == 128) stage_kernel_tc<128><<<grid, 128, smem, st>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t set_smem_tc(int Qp, size_t smem) {
+  if constexpr (P <= kTcMaxP) {
+    if (Qp == 256)
+      return cudaFuncSetAttribute(stage_kernel_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (Qp == 128)
+      return cudaFuncSetAttribute(stage_kernel_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  }
+  return cudaErrorInvalidValue;
+}
+
+int occupancy_tc(int Qp, size_t smem) {
+  int n = 0;
+  if constexpr (P <= kTcMaxP) {
+    if (Qp == 256) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel_tc<256>, 256, smem);
+    if (Qp == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel_tc<128>, 128, smem);
+  }
+  return n;
+}

@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("reduction", ctypes.c_int32), ("collision", ctypes.c_int32),
                 ("elems_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
-                ("pipeline_stages", ctypes.c_int32), ("test_wait_timeout", ctypes.c_int32)]
+                ("pipeline_stages", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
+                ("test_wait_timeout", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -54,6 +55,7 @@ class Info(ctypes.Structure):
                 ("eq_order", ctypes.c_int32), ("elems_per_cta", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("pipeline_stages", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("group", ctypes.c_int32), ("ngroups", ctypes.c_int32),
+                ("tensor_cores", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("state_bytes", ctypes.c_int64),
                 ("residual_bytes", ctypes.c_int64)]
 
@@ -100,6 +102,7 @@ SIGNATURES = {
     "fedbm_batch_info": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Info)]),
     "fedbm_batch_rk_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "fedbm_batch_set_tiles": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "fedbm_batch_set_tensor_cores": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "fedbm_batch_autotune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int32]),
     "fedbm_autotune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int32]),
 }
@@ -165,12 +168,14 @@ def velset_desc(kind=VELSET_GH, n=4, eq_order=2, nc_extent=4.0, nc_sqrt2=0):
 
 
 def params(kn=1.0, precision=FP32, reduction=RED_DEFAULT, cfl=0.5, dt=0.0, beta=1.0, collision=1,
-           length=1.0, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0, test_wait_timeout=0):
+           length=1.0, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0, tensor_cores=0,
+           test_wait_timeout=0):
     p = Params()
     p.kn, p.length, p.beta, p.cfl, p.dt = kn, length, beta, cfl, dt
     p.precision, p.reduction, p.collision = precision, reduction, collision
     p.elems_per_cta, p.threads_per_cta = elems_per_cta, threads_per_cta
     p.pipeline_stages = pipeline_stages
+    p.tensor_cores = tensor_cores
     p.test_wait_timeout = test_wait_timeout
     return p
 
@@ -311,6 +316,10 @@ def fedbm_batch_rk_step(h, nsteps=1):
 
 def fedbm_batch_set_tiles(h, group, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0):
     _check(lib().fedbm_batch_set_tiles(h, group, elems_per_cta, threads_per_cta, pipeline_stages))
+
+
+def fedbm_batch_set_tensor_cores(h, group, on=1):
+    _check(lib().fedbm_batch_set_tensor_cores(h, group, on))
 
 
 def fedbm_batch_autotune(h, cache_path=None, trials=0):

@@ -38,7 +38,8 @@ def descriptors(c, precision="fp32", reduction="default", **tile):
     prm = fb.params(kn=c.get("kn", 1.0), precision=PREC_CODE[precision], reduction=RED_CODE[reduction],
                     cfl=c.get("cfl", 0.5), beta=c.get("beta", 1.0), collision=int(c.get("collision", True)),
                     elems_per_cta=tile.get("epc", 0), threads_per_cta=tile.get("tpb", 0),
-                    pipeline_stages=tile.get("stages", 0), test_wait_timeout=tile.get("test_wait_timeout", 0))
+                    pipeline_stages=tile.get("stages", 0), tensor_cores=tile.get("tc", 0),
+                    test_wait_timeout=tile.get("test_wait_timeout", 0))
     return m, v, prm
 
 
