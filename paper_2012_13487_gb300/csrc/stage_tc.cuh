@@ -7,7 +7,7 @@
 // tensor memory).  Subtracting the first node's value f_0 changes nothing in
 // exact arithmetic (Dr 1 = Ds 1 = 0, the derivative of a constant) and keeps
 // the operands small.  Each FP32 operand x is split into x_hi = tf32(x) and
-// x_lo = tf32(x - x_hi) and every product is taken as
+// x_lo = x - x_hi (read by the MMA as TF32) and every product is taken as
 // a_hi b_hi + a_lo b_hi + a_hi b_lo (three MMAs), which keeps the contraction
 // error near FP32 rounding of the operands.
 //
@@ -38,9 +38,12 @@ __host__ __device__ constexpr int kidx(int r, int k, int KC) {
   return ((r >> 3) * KC + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
 }
 
-// Shared-memory layout (byte offsets) of one CTA.
+// Shared-memory layout (byte offsets) of one CTA.  Only the element's state
+// tile comes through shared memory (the node moments are reductions over all
+// velocities); each thread loads its own residual and neighbour-trace columns
+// into registers and writes its outputs from registers.
 struct Layout {
-  size_t bar, f, res, trF, A, B, L, geo, nbr, mom, wn, end;
+  size_t bar, f, A, F, B, L, geo, nbr, mom, wn, end;
 };
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline Layout layout(int QT) {
@@ -48,12 +51,10 @@ __host__ __device__ inline Layout layout(int QT) {
   size_t b = 0;
   o.bar = b;  b += 32;                                       // tile barrier, MMA barrier, TMEM address
   b = al(b, 128);
-  o.f = b;    b += size_t(NP) * QT * 4;                       // element tile (new state written back)
-  o.res = b;  b += size_t(NP) * QT * 4;                       // residual tile
+  o.f = b;    b += size_t(NP) * QT * 4;                       // element state tile
   b = al(b, 1024);
-  const size_t tr_bytes = size_t(NF) * QT * 4, fl_bytes = 2 * size_t(QT) * KL * 4;
-  o.trF = b;  b += al(tr_bytes > fl_bytes ? tr_bytes : fl_bytes, 1024);  // traces, then flux hi|lo
   o.A = b;    b += 2 * size_t(QT) * KD * 4;                   // (f - f_0) hi|lo
+  o.F = b;    b += 2 * size_t(QT) * KL * 4;                   // face fluxes hi|lo
   o.B = b;    b += 2 * size_t(2 * ND) * KD * 4;               // [Dr; Ds] hi|lo
   o.L = b;    b += 2 * size_t(NL) * KL * 4;                   // LIFT hi|lo
   o.geo = b;  b += al(kGeoStrideDev * 4, 16);
@@ -64,15 +65,17 @@ __host__ __device__ inline Layout layout(int QT) {
   return o;
 }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+// x rounded to the 10 explicit mantissa bits of TF32 (nearest, ties away from
+// zero in magnitude) by integer arithmetic on its bit pattern: add half a TF32
+// unit in the last place, clear the 13 low bits.  Finite |x| < 2^127 only.
+__device__ __forceinline__ uint32_t tf32_round_bits(float x) {
+  return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
-// x = hi + lo with hi, lo in TF32 (bit patterns)
+// x = hi + lo: hi in TF32, lo = x - hi exact in FP32 (|lo| <= 2^-11 |x|).  The
+// MMA reads the top 19 bits of lo, so the pair carries x to about 2^-21 |x|.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - __uint_as_float(hi));
+  hi = tf32_round_bits(x);
+  lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -147,8 +150,28 @@ __device__ __forceinline__ void put_row(float* hi, float* lo, int r, const float
 
 }  // namespace tc
 
+// Bulk copies of one element's state tile and geometry (warp 0); the lanes
+// also store its three face codes.  Every lane arrives on the barrier, so the
+// plain stores are visible to the threads that wait on it.
+__device__ __forceinline__ void tc_issue_tile(const StageArgs<float>& a, StageSmem<float, float>& sm, int QT,
+                                              int64_t k0) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 3) sm.nbr[lane] = __ldg(a.nbr + k0 * 3 + lane);
+  const uint32_t tile_bytes = uint32_t(NP * QT * 4), geo_bytes = uint32_t(kGeoStrideDev * 4);
+  mbar_arrive_expect_tx(sm.bar, lane == 0 ? tile_bytes + geo_bytes + a.extra_tx : 0u);
+  if (lane == 0) {
+    bulk_load(sm.f, static_cast<const float*>(a.f_in) + k0 * NP * QT, tile_bytes, sm.bar);
+    bulk_load(sm.geo, a.geo + k0 * kGeoStrideDev, geo_bytes, sm.bar);
+  }
+}
+
 // Persistent tensor-core stage kernel: CTA b handles elements b, b + gridDim.x,
-// ...; QT threads, thread t owns velocity t of the element throughout.
+// ...; QT threads, thread t owns velocity t of the element throughout.  Per
+// element: wait for the state tile; node moments and wall numerators from it;
+// each thread gathers its state, residual and neighbour traces, forms its face
+// fluxes and writes its operand rows; the state tile is then free and the
+// next element's copy starts while one thread issues the MMAs; the epilogue
+// reads the accumulators and writes the new state and residual.
 template <int QT>
 __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageArgs<float> a) {
   using ST = StoreF32;
@@ -161,14 +184,14 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
   uint64_t* bar_mma = bar_tile + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + o.bar + 16);
   float* sA = reinterpret_cast<float*>(smem + o.A);
-  float* sF = reinterpret_cast<float*>(smem + o.trF);
+  float* sF = reinterpret_cast<float*>(smem + o.F);
   float* sB = reinterpret_cast<float*>(smem + o.B);
   float* sL = reinterpret_cast<float*>(smem + o.L);
   StageSmem<float, float> sm;
   sm.bar = bar_tile;
   sm.f = reinterpret_cast<float*>(smem + o.f);
-  sm.res = reinterpret_cast<float*>(smem + o.res);
-  sm.tr = sF;
+  sm.res = nullptr;
+  sm.tr = nullptr;
   sm.geo = reinterpret_cast<float*>(smem + o.geo);
   sm.nbr = reinterpret_cast<int*>(smem + o.nbr);
   sm.scale = nullptr;
@@ -182,6 +205,8 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
   const bool read_res = rkA != 0.f;
   const bool third = a.eq_order == 3;
   const int64_t ntiles = a.K;  // one element per tile
+  const float* fin = static_cast<const float*>(a.f_in);
+  float* fout = static_cast<float*>(a.f_out);
 
   if (tid == 0) {
     mbar_init(bar_tile, 32);
@@ -199,16 +224,16 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
     const int nn = n < ND ? n : n - ND;
     double x = 0.0;
     if (nn < NP && m < NP) x = c_ops64[(n < ND ? OFF_DR : OFF_DS) + nn * NP + m];
-    const float h = __uint_as_float(tf32_rna(float(x)));
+    const float h = __uint_as_float(tf32_round_bits(float(x)));
     sB[kidx(n, m, KCD)] = h;
-    sB[2 * ND * KD + kidx(n, m, KCD)] = __uint_as_float(tf32_rna(float(x - double(h))));
+    sB[2 * ND * KD + kidx(n, m, KCD)] = float(x - double(h));
   }
   for (int v = tid; v < NL * KL; v += QT) {
     const int n = v / KL, j = v % KL;
     const double x = (n < NP && j < NF) ? c_ops64[OFF_LIFT + n * NF + j] : 0.0;
-    const float h = __uint_as_float(tf32_rna(float(x)));
+    const float h = __uint_as_float(tf32_round_bits(float(x)));
     sL[kidx(n, j, KCL)] = h;
-    sL[NL * KL + kidx(n, j, KCL)] = __uint_as_float(tf32_rna(float(x - double(h))));
+    sL[NL * KL + kidx(n, j, KCL)] = float(x - double(h));
   }
   fence_proxy_async_smem();
   fence_before_sync();
@@ -217,20 +242,34 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
   const uint32_t tmem = *tslot;
 
   int64_t tile = blockIdx.x;
-  if (tid < 32 && tile < ntiles) issue_tile_loads<ST, QT>(a, sm, tile, 1, read_res);
+  if (tid < 32 && tile < ntiles) tc_issue_tile(a, sm, QT, tile);
 
+  const int i = tid;
   const float* vel = a.vel;
-  const float ex = __ldg(vel + kVelEx * QT + tid), ey = __ldg(vel + kVelEy * QT + tid);
-  const float w = __ldg(vel + kVelW * QT + tid);
+  const float ex = __ldg(vel + kVelEx * QT + i), ey = __ldg(vel + kVelEy * QT + i);
+  const float w = __ldg(vel + kVelW * QT + i);
   const uint32_t sA_u = smem_u32(sA), sF_u = smem_u32(sF), sB_u = smem_u32(sB), sL_u = smem_u32(sL);
 
   bool failed = false;
+  int pending = -1;  // parity of a tile copy issued but not yet waited for
   for (int j = 0; tile < ntiles; ++j, tile += gridDim.x) {
     const int64_t k0 = tile;
-    if (j > 0 && tid < 32) {
-      if (tid == 0) bulk_wait_read();  // the previous tile's stores have read the buffers
-      __syncwarp();
-      issue_tile_loads<ST, QT>(a, sm, k0, 1, read_res);
+    // residual column and neighbour traces of this thread's velocity (in flight
+    // while the tile copy completes)
+    float rc[NP], tr[NF];
+#pragma unroll
+    for (int n = 0; n < NP; ++n) rc[n] = read_res ? __ldg(a.res + (k0 * NP + n) * QT + i) : 0.f;
+#pragma unroll
+    for (int fcx = 0; fcx < 3; ++fcx) {
+      const int code = __ldg(a.nbr + k0 * 3 + fcx);
+      const int64_t kn = code >= 0 ? int64_t(code >> 3) : k0;  // walls: an in-bounds address, not loaded
+      const int fn = (code >> 1) & 3;
+#pragma unroll
+      for (int aa = 0; aa < NFP; ++aa) {
+        const int a2 = (code & 1) ? NFP - 1 - aa : aa;
+        const int node = fn == 0 ? face_node(0, a2) : (fn == 1 ? face_node(1, a2) : face_node(2, a2));
+        tr[fcx * NFP + aa] = code >= 0 ? __ldg(fin + (kn * NP + node) * QT + i) : 0.f;
+      }
     }
     const bool ok = mbar_wait_bounded(bar_tile, uint32_t(j & 1), 2000000000ull);
     if (__syncthreads_or(!ok)) {
@@ -251,48 +290,48 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
     if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, 1);
     __syncthreads();
 
-    // ---- this thread's velocity: state column, residual column, face fluxes -------
-    const int i = tid;
+    // ---- this thread's velocity: state column, face fluxes, operand rows ----------
     const float* g = sm.geo;
     const float dt = g[kGeoDt], inv_tau = g[kGeoInvTau];
-    float fc[NP], rc[NP];
+    const float ar = ex * g[0] + ey * g[2], as = ex * g[1] + ey * g[3];
+    float fc[NP];
 #pragma unroll
-    for (int m = 0; m < NP; ++m) {
-      fc[m] = sm.f[m * QT + i];
-      rc[m] = read_res ? sm.res[m * QT + i] : 0.f;
-    }
-    float flux[NF];
+    for (int m = 0; m < NP; ++m) fc[m] = sm.f[m * QT + i];
+    {
+      float flux[NF];
 #pragma unroll
-    for (int fcx = 0; fcx < 3; ++fcx) {
-      const float en = ex * g[4 + 3 * fcx] + ey * g[5 + 3 * fcx];
-      const float c = 0.5f * (en - ab * fabsf(en)) * g[6 + 3 * fcx];
-      const int code = sm.nbr[fcx];
-      if (code >= 0) {
+      for (int fcx = 0; fcx < 3; ++fcx) {
+        const float en = ex * g[4 + 3 * fcx] + ey * g[5 + 3 * fcx];
+        const float c = 0.5f * (en - ab * fabsf(en)) * g[6 + 3 * fcx];
+        const int code = sm.nbr[fcx];
+        if (code >= 0) {
 #pragma unroll
-        for (int aa = 0; aa < NFP; ++aa)
-          flux[fcx * NFP + aa] = c * (fc[face_node(fcx, aa)] - sm.tr[(fcx * NFP + aa) * QT + i]);
-      } else {
-        const int slot = -code - 1;  // wall slot: 4 * case + side
-        const float fb = __ldg(a.wall_feq + slot * QT + i);
-        const float den_inv = __ldg(a.wall_den_inv + slot);
-        const bool diffuse = den_inv > 0.f;
-        const float scale = diffuse ? den_inv * fb : 0.f;
-        // incoming velocities take the wall state; outgoing ones have no jump
+          for (int aa = 0; aa < NFP; ++aa) flux[fcx * NFP + aa] = c * (fc[face_node(fcx, aa)] - tr[fcx * NFP + aa]);
+        } else {
+          const int slot = -code - 1;  // wall slot: 4 * case + side
+          const float fb = __ldg(a.wall_feq + slot * QT + i);
+          const float den_inv = __ldg(a.wall_den_inv + slot);
+          const bool diffuse = den_inv > 0.f;
+          const float scale = diffuse ? den_inv * fb : 0.f;
+          // incoming velocities take the wall state; outgoing ones have no jump
 #pragma unroll
-        for (int aa = 0; aa < NFP; ++aa) {
-          const float fp = diffuse ? sm.wn[fcx * NFP + aa] * scale : fb;
-          flux[fcx * NFP + aa] = en < 0.f ? c * (fc[face_node(fcx, aa)] - fp) : 0.f;
+          for (int aa = 0; aa < NFP; ++aa) {
+            const float fp = diffuse ? sm.wn[fcx * NFP + aa] * scale : fb;
+            flux[fcx * NFP + aa] = en < 0.f ? c * (fc[face_node(fcx, aa)] - fp) : 0.f;
+          }
         }
       }
+      put_row<KCD, NP>(sA, sA + QT * KD, i, fc, fc[0]);
+      put_row<KCL, NF>(sF, sF + QT * KL, i, flux, 0.f);
     }
-    __syncthreads();  // every trace has been read: the trace region takes the flux operand
-
-    // ---- operands, then the MMAs (one thread) --------------------------------------
-    put_row<KCD, NP>(sA, sA + QT * KD, i, fc, fc[0]);
-    put_row<KCL, NF>(sF, sF + QT * KL, i, flux, 0.f);
     fence_proxy_async_smem();
     fence_before_sync();
-    __syncthreads();
+    __syncthreads();  // operands written; the state tile, face codes and geometry are free
+
+    if (tile + gridDim.x < ntiles) {
+      if (tid < 32) tc_issue_tile(a, sm, QT, tile + gridDim.x);
+      pending = (j + 1) & 1;
+    }
     if (tid == 0) {
       fence_after_sync();
       constexpr uint32_t idD = idesc_tf32(128, 2 * ND), idL = idesc_tf32(128, NL);
@@ -330,9 +369,10 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
       failed = true;
       break;
     }
+    pending = -1;
     fence_after_sync();
 
-    // ---- epilogue: rhs, collision, update --------------------------------------------
+    // ---- epilogue: rhs, collision, update; outputs straight from registers ---------
     {
       const uint32_t ta = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t((warp >> 2) * CPM);
       float V[ND], W[ND], Lf[NL];
@@ -340,28 +380,24 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
       tmem_row<ND>(ta + ND, W);
       tmem_row<NL>(ta + 2 * ND, Lf);
       tmem_ld_wait();
-      const float ar = ex * g[0] + ey * g[2], as = ex * g[1] + ey * g[3];
 #pragma unroll
       for (int n = 0; n < NP; ++n) {
         float rhs = fmaf(-ar, V[n], fmaf(-as, W[n], Lf[n]));
         rhs += collision<float>(sm.mom + n * 8, ex, ey, w, fc[n], inv_tau, third);
         float r = dt * rhs;
         if (read_res) r = fmaf(rkA, rc[n], r);
-        sm.res[n * QT + i] = r;
-        sm.f[n * QT + i] = fmaf(rkB, r, fc[n]);
+        a.res[(k0 * NP + n) * QT + i] = r;
+        fout[(k0 * NP + n) * QT + i] = fmaf(rkB, r, fc[n]);
       }
     }
     fence_before_sync();
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      bulk_store(static_cast<float*>(a.f_out) + k0 * NP * QT, sm.f, uint32_t(NP * QT * 4));
-      bulk_store(a.res + k0 * NP * QT, sm.res, uint32_t(NP * QT * 4));
-      bulk_commit();
-    }
+    __syncthreads();  // node records and accumulators are free for the next element
   }
-  if (failed && tid == 0 && a.err) atomicExch(a.err, 1);
-  if (tid == 0) bulk_wait_read();
+  if (failed) {
+    if (tid == 0 && a.err) atomicExch(a.err, 1);
+    // a copy of the next tile may still be in flight: let it land (bounded)
+    if (pending >= 0) mbar_wait_bounded(bar_tile, uint32_t(pending), 1000000000ull);
+  }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -394,20 +430,40 @@ cudaError_t launch_tc(const void* args, int grid, size_t smem, cudaStream_t st) 
 }
 
 cudaError_t set_smem_tc(int Qp, size_t smem) {
+  auto set = [smem](auto kernel) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    // all of the SM's unified L1/shared storage as shared memory, so that
+    // several of these large tiles are resident at once
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  };
   if constexpr (P <= kTcMaxP) {
-    if (Qp == 256)
-      return cudaFuncSetAttribute(stage_kernel_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (Qp == 128)
-      return cudaFuncSetAttribute(stage_kernel_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (Qp == 256) return set(stage_kernel_tc<256>);
+    if (Qp == 128) return set(stage_kernel_tc<128>);
   }
   return cudaErrorInvalidValue;
 }
 
+// Resident CTAs per SM from the kernel's registers, its shared memory (with
+// the per-block reservation) and the thread limit.
 int occupancy_tc(int Qp, size_t smem) {
-  int n = 0;
   if constexpr (P <= kTcMaxP) {
-    if (Qp == 256) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel_tc<256>, 256, smem);
-    if (Qp == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel_tc<128>, 128, smem);
+    cudaFuncAttributes fa;
+    cudaError_t e = Qp == 256   ? cudaFuncGetAttributes(&fa, stage_kernel_tc<256>)
+                    : Qp == 128 ? cudaFuncGetAttributes(&fa, stage_kernel_tc<128>)
+                                : cudaErrorInvalidValue;
+    if (e != cudaSuccess) return 0;
+    int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
+    const int by_regs = regs_sm / (regs_warp * (Qp / 32));
+    const int by_smem = int(size_t(smem_sm) / (smem + fa.sharedSizeBytes + size_t(reserved)));
+    const int by_thr = thr_sm / Qp;
+    return std::min(by_regs, std::min(by_smem, by_thr));
   }
-  return n;
+  return 0;
 }
