@@ -114,8 +114,8 @@ typedef struct fedbm_params {
                             form has them and no tile is given above, else the
                             FMA kernel; 1 = tensor cores required (EINVAL where
                             the form has none); -1 = FMA kernel only.  The
-                            tensor-core form exists for FP32 state with 128 or
-                            256 padded velocities and degree <= 4           */
+                            tensor-core form exists for FP32 state with 128,
+                            256 or 1024 padded velocities and degree <= 4    */
   int32_t test_wait_timeout; /* test hook, keep 0: when 1, every stage kernel
                               waits for 16 bytes that never arrive, so its
                               bounded wait (about 3 s) runs out, the kernel

@@ -383,8 +383,8 @@ void drop_graphs(Batch& b) {
     }
 }
 
-// The tensor-core form of a group: one element per CTA, one thread per
-// velocity.  Each CTA holds tc_tmem_cols tensor-memory columns for its whole
+// The tensor-core form of a group: one element per CTA, 128 threads, one
+// velocity per thread in each 128-velocity pass.  Each CTA holds tc_tmem_cols tensor-memory columns for its whole
 // life; the resident CTAs of an SM must fit in its 512 columns so that an
 // allocation never waits on another CTA of the same kernel.
 int configure_tc(Batch& b, Group& g) {
@@ -406,7 +406,7 @@ int configure_tc(Batch& b, Group& g) {
     return fail(FEDBM_EINVAL, "tensor-core stage kernel cannot be resident within tensor memory");
   g.tc = 1;
   g.epc = 1;
-  g.tpb = g.Qp;
+  g.tpb = 128;  // one 128-velocity MMA tile per pass
   g.nstages = 1;
   g.smem = smem;
   g.grid = int(std::min<int64_t>(g.K, int64_t(per_sm) * nsm));

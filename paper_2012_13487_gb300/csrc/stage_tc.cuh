@@ -1,5 +1,5 @@
-// Tensor-core form of the stage kernel (FP32 state, QT = 128 or 256 velocities,
-// one velocity per thread).  Included by stage_impl.cuh inside its namespace:
+// Tensor-core form of the stage kernel (FP32 state, QT = 128, 256 or 1024
+// velocities, 128 threads, one velocity per thread in each 128-velocity pass).  Included by stage_impl.cuh inside its namespace:
 // it reuses the tile loads, node moments, wall numerators and collision term of
 // the FMA kernel and replaces the element-local contractions of phase 4,
 //   V = (f - f_0 1) Dr^T,  W = (f - f_0 1) Ds^T,  Lf = flux LIFT^T,
@@ -25,13 +25,11 @@ constexpr int ND = (NP + 15) / 16 * 16;   // N of one derivative operator (nodes
 constexpr int KL = (NF + 7) / 8 * 8;      // K of the lift MMA (face nodes)
 constexpr int NL = ND;                    // N of the lift MMA
 constexpr int KCD = KD / 4, KCL = KL / 4; // 16-byte chunks per operand row
-constexpr int CPM = 2 * ND + NL;          // accumulator columns per 128-velocity tile
+constexpr int CPM = 2 * ND + NL;          // accumulator columns of one 128-velocity pass
+constexpr int kTcThreads = 128;           // one MMA tile of velocities per pass
 
-// tensor-memory columns of one CTA: a power of two >= 32 covering every tile
-__host__ __device__ constexpr int ncols_for(int QT) {
-  return (QT / 128) * CPM <= 32 ? 32 : (QT / 128) * CPM <= 64 ? 64 : (QT / 128) * CPM <= 128 ? 128
-         : (QT / 128) * CPM <= 256 ? 256 : 512;
-}
+// tensor-memory columns of one CTA: a power of two >= 32
+constexpr int kTcCols = CPM <= 32 ? 32 : CPM <= 64 ? 64 : CPM <= 128 ? 128 : 256;
 
 // float index of (row r, column k) in a K-major operand with KC chunks per row
 __host__ __device__ constexpr int kidx(int r, int k, int KC) {
@@ -53,8 +51,8 @@ __host__ __device__ inline Layout layout(int QT) {
   b = al(b, 128);
   o.f = b;    b += size_t(NP) * QT * 4;                       // element state tile
   b = al(b, 1024);
-  o.A = b;    b += 2 * size_t(QT) * KD * 4;                   // (f - f_0) hi|lo
-  o.F = b;    b += 2 * size_t(QT) * KL * 4;                   // face fluxes hi|lo
+  o.A = b;    b += 2 * size_t(kTcThreads) * KD * 4;           // (f - f_0) hi|lo of one pass
+  o.F = b;    b += 2 * size_t(kTcThreads) * KL * 4;           // face fluxes hi|lo of one pass
   o.B = b;    b += 2 * size_t(2 * ND) * KD * 4;               // [Dr; Ds] hi|lo
   o.L = b;    b += 2 * size_t(NL) * KL * 4;                   // LIFT hi|lo
   o.geo = b;  b += al(kGeoStrideDev * 4, 16);
@@ -166,18 +164,19 @@ __device__ __forceinline__ void tc_issue_tile(const StageArgs<float>& a, StageSm
 }
 
 // Persistent tensor-core stage kernel: CTA b handles elements b, b + gridDim.x,
-// ...; QT threads, thread t owns velocity t of the element throughout.  Per
-// element: wait for the state tile; node moments and wall numerators from it;
-// each thread gathers its state, residual and neighbour traces, forms its face
-// fluxes and writes its operand rows; the state tile is then free and the
-// next element's copy starts while one thread issues the MMAs; the epilogue
-// reads the accumulators and writes the new state and residual.
+// ...  Per element: wait for the state tile; node moments and wall numerators
+// from it; then, for each pass of 128 velocities (thread t owns velocity
+// 128 pass + t), each thread gathers its state, residual and neighbour traces,
+// forms its face fluxes and writes its operand rows, one thread issues the
+// MMAs, and the epilogue reads the accumulators and writes the new state and
+// residual from registers.  Once the last pass has read the state tile, the
+// next element's copy starts and overlaps that pass's MMAs and epilogue.
 template <int QT>
-__global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageArgs<float> a) {
+__global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const StageArgs<float> a) {
   using ST = StoreF32;
   using namespace tc;
-  static_assert(QT == 128 || QT == 256, "one velocity per thread, whole 128-velocity MMA tiles");
-  constexpr int NCOLS = ncols_for(QT);
+  static_assert(QT % kTcThreads == 0, "whole 128-velocity passes");
+  constexpr int NPASS = QT / kTcThreads;
   extern __shared__ __align__(1024) unsigned char smem[];
   const Layout o = layout(QT);
   uint64_t* bar_tile = reinterpret_cast<uint64_t*>(smem + o.bar);
@@ -215,11 +214,11 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "n"(NCOLS));
+                 "n"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // B operands from the FP64 operators: [Dr; Ds] (rows n, then ND + n) and LIFT
-  for (int v = tid; v < 2 * ND * KD; v += QT) {
+  for (int v = tid; v < 2 * ND * KD; v += kTcThreads) {
     const int n = v / KD, m = v % KD;
     const int nn = n < ND ? n : n - ND;
     double x = 0.0;
@@ -228,7 +227,7 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
     sB[kidx(n, m, KCD)] = h;
     sB[2 * ND * KD + kidx(n, m, KCD)] = float(x - double(h));
   }
-  for (int v = tid; v < NL * KL; v += QT) {
+  for (int v = tid; v < NL * KL; v += kTcThreads) {
     const int n = v / KL, j = v % KL;
     const double x = (n < NP && j < NF) ? c_ops64[OFF_LIFT + n * NF + j] : 0.0;
     const float h = __uint_as_float(tf32_round_bits(float(x)));
@@ -244,42 +243,27 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
   int64_t tile = blockIdx.x;
   if (tid < 32 && tile < ntiles) tc_issue_tile(a, sm, QT, tile);
 
-  const int i = tid;
-  const float* vel = a.vel;
-  const float ex = __ldg(vel + kVelEx * QT + i), ey = __ldg(vel + kVelEy * QT + i);
-  const float w = __ldg(vel + kVelW * QT + i);
   const uint32_t sA_u = smem_u32(sA), sF_u = smem_u32(sF), sB_u = smem_u32(sB), sL_u = smem_u32(sL);
+  constexpr uint32_t idD = idesc_tf32(128, 2 * ND), idL = idesc_tf32(128, NL);
+  constexpr uint32_t aHalfD = kTcThreads * KD * 4, aHalfL = kTcThreads * KL * 4;  // hi -> lo bytes
+  constexpr uint32_t bHalfD = 2 * ND * KD * 4, bHalfL = NL * KL * 4;
+  const uint32_t ta = tmem + (uint32_t(32 * warp) << 16);  // this warp's accumulator lanes
 
   bool failed = false;
-  int pending = -1;  // parity of a tile copy issued but not yet waited for
+  int pending = -1;   // parity of a tile copy issued but not yet waited for
+  uint32_t mph = 0;   // phase of the MMA barrier
   for (int j = 0; tile < ntiles; ++j, tile += gridDim.x) {
     const int64_t k0 = tile;
-    // residual column and neighbour traces of this thread's velocity (in flight
-    // while the tile copy completes)
-    float rc[NP], tr[NF];
-#pragma unroll
-    for (int n = 0; n < NP; ++n) rc[n] = read_res ? __ldg(a.res + (k0 * NP + n) * QT + i) : 0.f;
-#pragma unroll
-    for (int fcx = 0; fcx < 3; ++fcx) {
-      const int code = __ldg(a.nbr + k0 * 3 + fcx);
-      const int64_t kn = code >= 0 ? int64_t(code >> 3) : k0;  // walls: an in-bounds address, not loaded
-      const int fn = (code >> 1) & 3;
-#pragma unroll
-      for (int aa = 0; aa < NFP; ++aa) {
-        const int a2 = (code & 1) ? NFP - 1 - aa : aa;
-        const int node = fn == 0 ? face_node(0, a2) : (fn == 1 ? face_node(1, a2) : face_node(2, a2));
-        tr[fcx * NFP + aa] = code >= 0 ? __ldg(fin + (kn * NP + node) * QT + i) : 0.f;
-      }
-    }
     const bool ok = mbar_wait_bounded(bar_tile, uint32_t(j & 1), 2000000000ull);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
+    pending = -1;
 
     // ---- node moments and wall numerators (as in the FMA kernel) -----------------
     if (!a.collision) {
-      for (int v = tid; v < NP * 8; v += QT) sm.mom[v] = 0.f;
+      for (int v = tid; v < NP * 8; v += kTcThreads) sm.mom[v] = 0.f;
     } else if (a.red == kRedFP64) {
       tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1);
     } else if (a.red == kRedCompFP32) {
@@ -289,109 +273,116 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
     }
     if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, 1);
     __syncthreads();
+    const float dt = sm.geo[kGeoDt], inv_tau = sm.geo[kGeoInvTau];
+    float gl[13];  // rx, sx, ry, sy and (nx, ny, Fscale) of the three faces
+#pragma unroll
+    for (int q = 0; q < 13; ++q) gl[q] = sm.geo[q];
+    int codes[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) codes[q] = sm.nbr[q];
 
-    // ---- this thread's velocity: state column, face fluxes, operand rows ----------
-    const float* g = sm.geo;
-    const float dt = g[kGeoDt], inv_tau = g[kGeoInvTau];
-    const float ar = ex * g[0] + ey * g[2], as = ex * g[1] + ey * g[3];
-    float fc[NP];
+    for (int pass = 0; pass < NPASS; ++pass) {
+      const int i = pass * kTcThreads + tid;
+      const float ex = __ldg(a.vel + kVelEx * QT + i), ey = __ldg(a.vel + kVelEy * QT + i);
+      const float w = __ldg(a.vel + kVelW * QT + i);
+      float rc[NP], fc[NP];
 #pragma unroll
-    for (int m = 0; m < NP; ++m) fc[m] = sm.f[m * QT + i];
-    {
-      float flux[NF];
+      for (int n = 0; n < NP; ++n) rc[n] = read_res ? __ldg(a.res + (k0 * NP + n) * QT + i) : 0.f;
 #pragma unroll
-      for (int fcx = 0; fcx < 3; ++fcx) {
-        const float en = ex * g[4 + 3 * fcx] + ey * g[5 + 3 * fcx];
-        const float c = 0.5f * (en - ab * fabsf(en)) * g[6 + 3 * fcx];
-        const int code = sm.nbr[fcx];
-        if (code >= 0) {
+      for (int m = 0; m < NP; ++m) fc[m] = sm.f[m * QT + i];
+      {
+        float flux[NF];
 #pragma unroll
-          for (int aa = 0; aa < NFP; ++aa) flux[fcx * NFP + aa] = c * (fc[face_node(fcx, aa)] - tr[fcx * NFP + aa]);
-        } else {
-          const int slot = -code - 1;  // wall slot: 4 * case + side
-          const float fb = __ldg(a.wall_feq + slot * QT + i);
-          const float den_inv = __ldg(a.wall_den_inv + slot);
-          const bool diffuse = den_inv > 0.f;
-          const float scale = diffuse ? den_inv * fb : 0.f;
-          // incoming velocities take the wall state; outgoing ones have no jump
+        for (int fcx = 0; fcx < 3; ++fcx) {
+          const float en = ex * gl[4 + 3 * fcx] + ey * gl[5 + 3 * fcx];
+          const float c = 0.5f * (en - ab * fabsf(en)) * gl[6 + 3 * fcx];
+          const int code = codes[fcx];
+          if (code >= 0) {
+            const int64_t kn = code >> 3;
+            const int fn = (code >> 1) & 3;
 #pragma unroll
-          for (int aa = 0; aa < NFP; ++aa) {
-            const float fp = diffuse ? sm.wn[fcx * NFP + aa] * scale : fb;
-            flux[fcx * NFP + aa] = en < 0.f ? c * (fc[face_node(fcx, aa)] - fp) : 0.f;
+            for (int aa = 0; aa < NFP; ++aa) {
+              const int a2 = (code & 1) ? NFP - 1 - aa : aa;
+              const int node = fn == 0 ? face_node(0, a2) : (fn == 1 ? face_node(1, a2) : face_node(2, a2));
+              flux[fcx * NFP + aa] = c * (fc[face_node(fcx, aa)] - __ldg(fin + (kn * NP + node) * QT + i));
+            }
+          } else {
+            const int slot = -code - 1;  // wall slot: 4 * case + side
+            const float fb = __ldg(a.wall_feq + slot * QT + i);
+            const float den_inv = __ldg(a.wall_den_inv + slot);
+            const bool diffuse = den_inv > 0.f;
+            const float scale = diffuse ? den_inv * fb : 0.f;
+            // incoming velocities take the wall state; outgoing ones have no jump
+#pragma unroll
+            for (int aa = 0; aa < NFP; ++aa) {
+              const float fp = diffuse ? sm.wn[fcx * NFP + aa] * scale : fb;
+              flux[fcx * NFP + aa] = en < 0.f ? c * (fc[face_node(fcx, aa)] - fp) : 0.f;
+            }
           }
         }
+        put_row<KCD, NP>(sA, sA + kTcThreads * KD, tid, fc, fc[0]);
+        put_row<KCL, NF>(sF, sF + kTcThreads * KL, tid, flux, 0.f);
       }
-      put_row<KCD, NP>(sA, sA + QT * KD, i, fc, fc[0]);
-      put_row<KCL, NF>(sF, sF + QT * KL, i, flux, 0.f);
-    }
-    fence_proxy_async_smem();
-    fence_before_sync();
-    __syncthreads();  // operands written; the state tile, face codes and geometry are free
+      fence_proxy_async_smem();
+      fence_before_sync();
+      __syncthreads();  // operand rows written (and, in the last pass, the state tile read)
 
-    if (tile + gridDim.x < ntiles) {
-      if (tid < 32) tc_issue_tile(a, sm, QT, tile + gridDim.x);
-      pending = (j + 1) & 1;
-    }
-    if (tid == 0) {
-      fence_after_sync();
-      constexpr uint32_t idD = idesc_tf32(128, 2 * ND), idL = idesc_tf32(128, NL);
-      constexpr uint32_t aHalfD = QT * KD * 4, aHalfL = QT * KL * 4;  // hi -> lo bytes
-      constexpr uint32_t bHalfD = 2 * ND * KD * 4, bHalfL = NL * KL * 4;
-#pragma unroll
-      for (int mt = 0; mt < QT / 128; ++mt) {
-        const uint32_t d = tmem + uint32_t(mt * CPM);
-        const uint32_t aoD = uint32_t(mt * 16 * KCD * 128), aoL = uint32_t(mt * 16 * KCL * 128);
+      if (pass == NPASS - 1 && tile + gridDim.x < ntiles) {
+        if (tid < 32) tc_issue_tile(a, sm, QT, tile + gridDim.x);
+        pending = (j + 1) & 1;
+      }
+      if (tid == 0) {
+        fence_after_sync();
 #pragma unroll
         for (int ks = 0; ks < KD / 8; ++ks) {
           const uint32_t ko = uint32_t(ks * 256);
-          const uint64_t ah = sdesc(sA_u + aoD + ko, 128, KCD * 128);
-          const uint64_t al = sdesc(sA_u + aHalfD + aoD + ko, 128, KCD * 128);
+          const uint64_t ah = sdesc(sA_u + ko, 128, KCD * 128), al = sdesc(sA_u + aHalfD + ko, 128, KCD * 128);
           const uint64_t bh = sdesc(sB_u + ko, 128, KCD * 128), bl = sdesc(sB_u + bHalfD + ko, 128, KCD * 128);
-          mma_tf32(d, ah, bh, idD, ks > 0);
-          mma_tf32(d, al, bh, idD, 1);
-          mma_tf32(d, ah, bl, idD, 1);
+          mma_tf32(tmem, ah, bh, idD, ks > 0);
+          mma_tf32(tmem, al, bh, idD, 1);
+          mma_tf32(tmem, ah, bl, idD, 1);
         }
 #pragma unroll
         for (int ks = 0; ks < KL / 8; ++ks) {
           const uint32_t ko = uint32_t(ks * 256);
-          const uint64_t ah = sdesc(sF_u + aoL + ko, 128, KCL * 128);
-          const uint64_t al = sdesc(sF_u + aHalfL + aoL + ko, 128, KCL * 128);
+          const uint64_t ah = sdesc(sF_u + ko, 128, KCL * 128), al = sdesc(sF_u + aHalfL + ko, 128, KCL * 128);
           const uint64_t bh = sdesc(sL_u + ko, 128, KCL * 128), bl = sdesc(sL_u + bHalfL + ko, 128, KCL * 128);
-          mma_tf32(d + 2 * ND, ah, bh, idL, ks > 0);
-          mma_tf32(d + 2 * ND, al, bh, idL, 1);
-          mma_tf32(d + 2 * ND, ah, bl, idL, 1);
+          mma_tf32(tmem + 2 * ND, ah, bh, idL, ks > 0);
+          mma_tf32(tmem + 2 * ND, al, bh, idL, 1);
+          mma_tf32(tmem + 2 * ND, ah, bl, idL, 1);
+        }
+        mma_commit(bar_mma);
+      }
+      const bool mok = mbar_wait_bounded(bar_mma, mph, 2000000000ull);
+      mph ^= 1u;
+      if (__syncthreads_or(!mok)) {
+        failed = true;
+        break;
+      }
+      fence_after_sync();
+
+      // ---- epilogue: rhs, collision, update; outputs straight from registers -------
+      {
+        float V[ND], W[ND], Lf[NL];
+        tmem_row<ND>(ta, V);
+        tmem_row<ND>(ta + ND, W);
+        tmem_row<NL>(ta + 2 * ND, Lf);
+        tmem_ld_wait();
+        const float ar = ex * gl[0] + ey * gl[2], as = ex * gl[1] + ey * gl[3];
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          float rhs = fmaf(-ar, V[n], fmaf(-as, W[n], Lf[n]));
+          rhs += collision<float>(sm.mom + n * 8, ex, ey, w, fc[n], inv_tau, third);
+          float r = dt * rhs;
+          if (read_res) r = fmaf(rkA, rc[n], r);
+          a.res[(k0 * NP + n) * QT + i] = r;
+          fout[(k0 * NP + n) * QT + i] = fmaf(rkB, r, fc[n]);
         }
       }
-      mma_commit(bar_mma);
+      fence_before_sync();
+      __syncthreads();  // accumulators and operand rows are free for the next pass
     }
-    const bool mok = mbar_wait_bounded(bar_mma, uint32_t(j & 1), 2000000000ull);
-    if (__syncthreads_or(!mok)) {
-      failed = true;
-      break;
-    }
-    pending = -1;
-    fence_after_sync();
-
-    // ---- epilogue: rhs, collision, update; outputs straight from registers ---------
-    {
-      const uint32_t ta = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t((warp >> 2) * CPM);
-      float V[ND], W[ND], Lf[NL];
-      tmem_row<ND>(ta, V);
-      tmem_row<ND>(ta + ND, W);
-      tmem_row<NL>(ta + 2 * ND, Lf);
-      tmem_ld_wait();
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        float rhs = fmaf(-ar, V[n], fmaf(-as, W[n], Lf[n]));
-        rhs += collision<float>(sm.mom + n * 8, ex, ey, w, fc[n], inv_tau, third);
-        float r = dt * rhs;
-        if (read_res) r = fmaf(rkA, rc[n], r);
-        a.res[(k0 * NP + n) * QT + i] = r;
-        fout[(k0 * NP + n) * QT + i] = fmaf(rkB, r, fc[n]);
-      }
-    }
-    fence_before_sync();
-    __syncthreads();  // node records and accumulators are free for the next element
+    if (failed) break;
   }
   if (failed) {
     if (tid == 0 && a.err) atomicExch(a.err, 1);
@@ -402,7 +393,7 @@ __global__ void __launch_bounds__(QT, 256 / QT * 2) stage_kernel_tc(const StageA
   __syncthreads();
   if (warp == 0) {
     fence_after_sync();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(NCOLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcCols));
   }
 }
 
@@ -411,59 +402,59 @@ constexpr int kTcMaxP = 4;
 
 // Dynamic shared memory of the tensor-core kernel (0 = no tensor-core form).
 size_t tc_smem(int store_kind, int Qp) {
-  if (P > kTcMaxP || store_kind != kStoreF32 || (Qp != 128 && Qp != 256)) return 0;
+  if (P > kTcMaxP || store_kind != kStoreF32 || (Qp != 128 && Qp != 256 && Qp != 1024)) return 0;
   return tc::layout(Qp).end;
 }
 
 // Tensor-memory columns one CTA of the tensor-core kernel allocates.
-int tc_tmem_cols(int Qp) { return tc::ncols_for(Qp); }
+int tc_tmem_cols(int) { return tc::kTcCols; }
 
 cudaError_t launch_tc(const void* args, int grid, size_t smem, cudaStream_t st) {
   if constexpr (P <= kTcMaxP) {
     const auto& a = *static_cast<const StageArgs<float>*>(args);
-    if (a.Qp == 256) stage_kernel_tc<256><<<grid, 256, smem, st>>>(a);
-    else if (a.Qp == 128) stage_kernel_tc<128><<<grid, 128, smem, st>>>(a);
+    if (a.Qp == 256) stage_kernel_tc<256><<<grid, tc::kTcThreads, smem, st>>>(a);
+    else if (a.Qp == 128) stage_kernel_tc<128><<<grid, tc::kTcThreads, smem, st>>>(a);
+    else if (a.Qp == 1024) stage_kernel_tc<1024><<<grid, tc::kTcThreads, smem, st>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
 }
 
+template <class Fn>
+cudaError_t with_tc_kernel(int Qp, Fn fn) {
+  if constexpr (P <= kTcMaxP) {
+    if (Qp == 256) return fn(stage_kernel_tc<256>);
+    if (Qp == 128) return fn(stage_kernel_tc<128>);
+    if (Qp == 1024) return fn(stage_kernel_tc<1024>);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t set_smem_tc(int Qp, size_t smem) {
-  auto set = [smem](auto kernel) {
+  return with_tc_kernel(Qp, [smem](auto kernel) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     // all of the SM's unified L1/shared storage as shared memory, so that
-    // several of these large tiles are resident at once
+    // several of these tiles are resident at once
     return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  };
-  if constexpr (P <= kTcMaxP) {
-    if (Qp == 256) return set(stage_kernel_tc<256>);
-    if (Qp == 128) return set(stage_kernel_tc<128>);
-  }
-  return cudaErrorInvalidValue;
+  });
 }
 
 // Resident CTAs per SM from the kernel's registers, its shared memory (with
 // the per-block reservation) and the thread limit.
 int occupancy_tc(int Qp, size_t smem) {
-  if constexpr (P <= kTcMaxP) {
-    cudaFuncAttributes fa;
-    cudaError_t e = Qp == 256   ? cudaFuncGetAttributes(&fa, stage_kernel_tc<256>)
-                    : Qp == 128 ? cudaFuncGetAttributes(&fa, stage_kernel_tc<128>)
-                                : cudaErrorInvalidValue;
-    if (e != cudaSuccess) return 0;
-    int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, reserved = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
-    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
-    const int by_regs = regs_sm / (regs_warp * (Qp / 32));
-    const int by_smem = int(size_t(smem_sm) / (smem + fa.sharedSizeBytes + size_t(reserved)));
-    const int by_thr = thr_sm / Qp;
-    return std::min(by_regs, std::min(by_smem, by_thr));
-  }
-  return 0;
+  cudaFuncAttributes fa;
+  if (with_tc_kernel(Qp, [&fa](auto kernel) { return cudaFuncGetAttributes(&fa, kernel); }) != cudaSuccess) return 0;
+  int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
+  const int by_regs = regs_sm / (regs_warp * (tc::kTcThreads / 32));
+  const int by_smem = int(size_t(smem_sm) / (smem + fa.sharedSizeBytes + size_t(reserved)));
+  const int by_thr = thr_sm / tc::kTcThreads;
+  return std::min(by_regs, std::min(by_smem, by_thr));
 }

@@ -1,7 +1,7 @@
 """Tensor-core form of the stage kernel (tcgen05 TF32 MMAs with a hi/lo split
 for the Dr, Ds and LIFT contractions) against the FP64 oracle and against the
-FMA form, on the shapes it serves: FP32 state, 128 or 256 padded velocities,
-degree <= 4."""
+FMA form, on the shapes it serves: FP32 state, 128, 256 or 1024 padded
+velocities, degree <= 4."""
 import numpy as np
 import pytest
 
@@ -29,7 +29,7 @@ def _pair(c, nsteps, amp=1e-2, seed=17, reduction="default", **tile):
 def test_tc_cavity_nc16_matches_oracle_and_fma(p):
     c = cases.cavity(5, 4, p, velset=("nc", 16), kn=1.0)
     pr, s, f0, f_tc = _pair(c, 6, tc=1)
-    assert s.info.tensor_cores == 1 and s.info.threads_per_cta == 256 and s.info.elems_per_cta == 1
+    assert s.info.tensor_cores == 1 and s.info.threads_per_cta == 128 and s.info.elems_per_cta == 1
     f_or = pr.run(f0, 6)
     assert cases.rel_max_err(f_tc, f_or) < fp32_tol(pr, 30)
     _, s2, _, f_fma = _pair(c, 6, tc=-1)
@@ -44,6 +44,15 @@ def test_tc_128_velocities_couette_eq3_usedbc_central():
     pr, s, f0, f_tc = _pair(c, 8, tc=1)
     assert s.info.tensor_cores == 1 and s.info.Q_padded == 128 and s.info.threads_per_cta == 128
     assert cases.rel_max_err(f_tc, pr.run(f0, 8)) < fp32_tol(pr, 40)
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_tc_1024_velocities_cavity_kn8(p):
+    # NC 32x32: eight 128-velocity passes per element
+    c = cases.cavity(3, 3, p, velset=("nc", 32), kn=8.0)
+    pr, s, f0, f_tc = _pair(c, 3, tc=1)
+    assert s.info.tensor_cores == 1 and s.info.Q_padded == 1024
+    assert cases.rel_max_err(f_tc, pr.run(f0, 3)) < fp32_tol(pr, 15)
 
 
 def test_tc_default_selection_and_rejection():
