@@ -86,7 +86,7 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 
 // Shared-memory layout of one stage CTA (offsets in bytes); the host sizes the
 // launch with it and the kernel carves its buffers with it.
-enum SmemPart { kSmBar, kSmF, kSmRes, kSmTr, kSmGeo, kSmNbr, kSmScale, kSmNScale, kSmDmax, kSmMom, kSmWn, kSmEnd };
+enum SmemPart { kSmBar, kSmF, kSmRes, kSmTr, kSmGeo, kSmNbr, kSmScale, kSmNScale, kSmDmax, kSmMom, kSmWn, kSmVel, kSmEnd };
 
 __host__ __device__ inline size_t stage_smem_layout(int Np, int NF, int epc, int Qp, size_t s_bytes, size_t r_bytes,
                                                     size_t off[kSmEnd + 1]) {
@@ -102,6 +102,7 @@ __host__ __device__ inline size_t stage_smem_layout(int Np, int NF, int epc, int
   off[kSmDmax] = b;   b += align16(size_t(epc) * 4);
   off[kSmMom] = b;    b += align16(size_t(epc) * Np * 8 * r_bytes);   // f^eq/tau coefficients per node
   off[kSmWn] = b;     b += align16(size_t(epc) * NF * r_bytes);        // wall numerators
+  off[kSmVel] = b;    b += align16(size_t(3) * Qp * r_bytes);          // e_x, e_y, w rows (copied once)
   off[kSmEnd] = b;
   return b;
 }
@@ -119,6 +120,7 @@ struct StageSmem {
   unsigned* dmax;
   R* mom;
   R* wn;
+  R* vel;  // e_x, e_y, w: three rows of Qp
 };
 
 template <typename R, typename S>
@@ -137,6 +139,7 @@ __device__ inline StageSmem<R, S> carve_stage_smem(unsigned char* base, int Np, 
   s.dmax = reinterpret_cast<unsigned*>(base + off[kSmDmax]);
   s.mom = reinterpret_cast<R*>(base + off[kSmMom]);
   s.wn = reinterpret_cast<R*>(base + off[kSmWn]);
+  s.vel = reinterpret_cast<R*>(base + off[kSmVel]);
   return s;
 }
 

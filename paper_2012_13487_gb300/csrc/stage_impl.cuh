@@ -213,7 +213,8 @@ struct Vec16 {
 // node; each lane reduces 16-byte chunks of the node's velocity row.
 template <class ST, class Acc, int QT>
 __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename ST::S* s_f,
-                             const float* s_scale, const typename ST::R* s_geo, typename ST::R* s_mom, int ne) {
+                             const float* s_scale, const typename ST::R* s_geo, typename ST::R* s_mom, int ne,
+                             const typename ST::R* s_vel) {
   using R = typename ST::R;
   using S = typename ST::S;
   constexpr int V = Vec16<ST>::N;
@@ -223,9 +224,9 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
   while (G > 1 && G > nchunk) G >>= 1;
   const int ngroups = nth / G, grp = tid / G, lane = tid % G;
   const int npair = ne * NP;
-  const R* ex = a.vel + kVelEx * Qp;
-  const R* ey = a.vel + kVelEy * Qp;
-  const R* wv = a.vel + kVelW * Qp;
+  const R* ex = s_vel + kVelEx * Qp;  // shared-memory copy of the velocity rows
+  const R* ey = s_vel + kVelEy * Qp;
+  const R* wv = s_vel + kVelW * Qp;
   for (int base = 0; base < npair; base += ngroups) {
     const int pair = base + grp;
     const bool valid = pair < npair;
@@ -238,9 +239,9 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
         *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(row + c * V);
 #pragma unroll
         for (int j = 0; j < V * int(sizeof(R)) / 16; ++j) {
-          reinterpret_cast<uint4*>(exv)[j] = __ldg(reinterpret_cast<const uint4*>(ex + c * V) + j);
-          reinterpret_cast<uint4*>(eyv)[j] = __ldg(reinterpret_cast<const uint4*>(ey + c * V) + j);
-          if constexpr (ST::dev) reinterpret_cast<uint4*>(wvv)[j] = __ldg(reinterpret_cast<const uint4*>(wv + c * V) + j);
+          reinterpret_cast<uint4*>(exv)[j] = reinterpret_cast<const uint4*>(ex + c * V)[j];
+          reinterpret_cast<uint4*>(eyv)[j] = reinterpret_cast<const uint4*>(ey + c * V)[j];
+          if constexpr (ST::dev) reinterpret_cast<uint4*>(wvv)[j] = reinterpret_cast<const uint4*>(wv + c * V)[j];
         }
         // sums over the chunk in the compute precision, then one accumulator
         // update per chunk (FP64 or compensated across chunks)
@@ -299,15 +300,16 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
 template <class ST, int QT>
 __device__ void tile_wall_numerators(const StageArgs<typename ST::R>& a, const typename ST::S* s_f,
                                      const typename ST::R* s_geo, const int* s_nbr,
-                                     const float* s_scale, typename ST::R* s_wn, int ne) {
+                                     const float* s_scale, typename ST::R* s_wn, int ne,
+                                     const typename ST::R* s_vel) {
   using R = typename ST::R;
   const int Qp = QT > 0 ? QT : a.Qp, tid = threadIdx.x, nth = blockDim.x;
   const int G = pow2_floor_32(nth / (a.epc * NF));
   const int ngroups = nth / G, grp = tid / G, lane = tid % G;
   const int ntrip = ne * NF;
-  const R* ex = a.vel + kVelEx * Qp;
-  const R* ey = a.vel + kVelEy * Qp;
-  const R* wv = a.vel + kVelW * Qp;
+  const R* ex = s_vel + kVelEx * Qp;  // shared-memory copy of the velocity rows
+  const R* ey = s_vel + kVelEy * Qp;
+  const R* wv = s_vel + kVelW * Qp;
   for (int base = 0; base < ntrip; base += ngroups) {
     const int trip = base + grp;
     const int e = trip / NF, fc = (trip % NF) / NFP, aa = trip % NFP;
@@ -325,8 +327,8 @@ __device__ void tile_wall_numerators(const StageArgs<typename ST::R>& a, const t
       const typename ST::S* row = s_f + (size_t(e) * NP + node) * Qp;
       const R sc = ST::dev ? s_scale[e] : R(0);
       for (int i = lane; i < Qp; i += G) {
-        const R en = __ldg(ex + i) * nxf + __ldg(ey + i) * nyf;
-        const R w = __ldg(wv + i);
+        const R en = ex[i] * nxf + ey[i] * nyf;
+        const R w = ST::dev ? wv[i] : R(0);  // the plain forms do not use (or hold) the w row
         if (en > 0) acc += en * decode<ST>(row[i], w, w * sc);
       }
     }
@@ -610,6 +612,12 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
   const size_t row_bytes = size_t(Qp) * sizeof(S);
 
   const bool two = a.nstages == 2;
+  // velocity rows e_x, e_y, w into every stage's copy (read by the moment and
+  // wall-numerator reductions)
+  for (int sidx = 0; sidx < (two ? 2 : 1); ++sidx) {
+    R* sv = stage(sidx).vel;
+    for (int v = tid; v < 3 * Qp; v += nth) sv[v] = a.vel[v];
+  }
   if (tid == 0) {
     mbar_init(stage(0).bar, 32);
     if (two) mbar_init(stage(1).bar, 32);  // the second stage exists only when nstages == 2
@@ -657,15 +665,15 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
       for (int v = tid; v < ne * NP * 8; v += nth) sm.mom[v] = R(0);
     } else {
       if constexpr (sizeof(R) == 8) {
-        tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne);
+        tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
       } else {
-        if (a.red == kRedFP64) tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne);
-        else if (a.red == kRedCompFP32) tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne);
-        else tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne);
+        if (a.red == kRedFP64) tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
+        else if (a.red == kRedCompFP32) tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
+        else tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
       }
     }
     // ---- 3. wall numerators ------------------------------------------------------
-    if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, ne);
+    if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, ne, sm.vel);
     __syncthreads();
 
     // ---- 4. residual and update ----------------------------------------------------

@@ -41,7 +41,7 @@ __host__ __device__ constexpr int kidx(int r, int k, int KC) {
 // velocities); each thread loads its own residual and neighbour-trace columns
 // into registers and writes its outputs from registers.
 struct Layout {
-  size_t bar, f, A, F, B, L, geo, nbr, mom, wn, end;
+  size_t bar, f, A, F, B, L, geo, nbr, mom, wn, vel, end;
 };
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline Layout layout(int QT) {
@@ -50,7 +50,7 @@ __host__ __device__ inline Layout layout(int QT) {
   o.bar = b;  b += 32;                                       // tile barrier, MMA barrier, TMEM address
   b = al(b, 128);
   o.f = b;    b += size_t(NP) * QT * 4;                       // element state tile
-  b = al(b, 1024);
+  b = al(b, 128);
   o.A = b;    b += 2 * size_t(kTcThreads) * KD * 4;           // (f - f_0) hi|lo of one pass
   o.F = b;    b += 2 * size_t(kTcThreads) * KL * 4;           // face fluxes hi|lo of one pass
   o.B = b;    b += 2 * size_t(2 * ND) * KD * 4;               // [Dr; Ds] hi|lo
@@ -59,6 +59,7 @@ __host__ __device__ inline Layout layout(int QT) {
   o.nbr = b;  b += 16;
   o.mom = b;  b += al(size_t(NP) * 8 * 4, 16);
   o.wn = b;   b += al(size_t(NF) * 4, 16);
+  o.vel = b;  b += al(size_t(2) * QT * 4, 16);              // e_x, e_y rows (the FP32 paths read no w row)
   o.end = b;
   return o;
 }
@@ -111,6 +112,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
       : "r"(taddr));
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+// 8 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -177,7 +187,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   using namespace tc;
   static_assert(QT % kTcThreads == 0, "whole 128-velocity passes");
   constexpr int NPASS = QT / kTcThreads;
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];  // operands need 16-byte alignment
   const Layout o = layout(QT);
   uint64_t* bar_tile = reinterpret_cast<uint64_t*>(smem + o.bar);
   uint64_t* bar_mma = bar_tile + 1;
@@ -198,6 +208,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   sm.dmax = nullptr;
   sm.mom = reinterpret_cast<float*>(smem + o.mom);
   sm.wn = reinterpret_cast<float*>(smem + o.wn);
+  sm.vel = reinterpret_cast<float*>(smem + o.vel);
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const float rkA = a.rkA, rkB = a.rkB, ab = a.ab;
@@ -217,6 +228,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
                  "n"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  for (int v = tid; v < 2 * QT; v += kTcThreads) sm.vel[v] = a.vel[v];
   // B operands from the FP64 operators: [Dr; Ds] (rows n, then ND + n) and LIFT
   for (int v = tid; v < 2 * ND * KD; v += kTcThreads) {
     const int n = v / KD, m = v % KD;
@@ -249,6 +261,27 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   constexpr uint32_t bHalfD = 2 * ND * KD * 4, bHalfL = NL * KL * 4;
   const uint32_t ta = tmem + (uint32_t(32 * warp) << 16);  // this warp's accumulator lanes
 
+  // residual and neighbour-trace columns of (element k, velocity i), loaded
+  // one pass ahead of their use
+  auto fetch = [&](int64_t k, int i, float (&rx)[NP], float (&tx)[NF]) {
+#pragma unroll
+    for (int n = 0; n < NP; ++n) rx[n] = read_res ? __ldg(a.res + (k * NP + n) * QT + i) : 0.f;
+#pragma unroll
+    for (int fcx = 0; fcx < 3; ++fcx) {
+      const int code = __ldg(a.nbr + k * 3 + fcx);
+      const int64_t kn = code >= 0 ? int64_t(code >> 3) : k;  // walls: an in-bounds address, not used
+      const int fn = (code >> 1) & 3;
+#pragma unroll
+      for (int aa = 0; aa < NFP; ++aa) {
+        const int a2 = (code & 1) ? NFP - 1 - aa : aa;
+        const int node = fn == 0 ? face_node(0, a2) : (fn == 1 ? face_node(1, a2) : face_node(2, a2));
+        tx[fcx * NFP + aa] = code >= 0 ? __ldg(fin + (kn * NP + node) * QT + i) : 0.f;
+      }
+    }
+  };
+  float rcur[NP], tcur[NF];
+  if (tile < ntiles) fetch(tile, tid, rcur, tcur);
+
   bool failed = false;
   int pending = -1;   // parity of a tile copy issued but not yet waited for
   uint32_t mph = 0;   // phase of the MMA barrier
@@ -265,47 +298,35 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
     if (!a.collision) {
       for (int v = tid; v < NP * 8; v += kTcThreads) sm.mom[v] = 0.f;
     } else if (a.red == kRedFP64) {
-      tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1);
+      tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
     } else if (a.red == kRedCompFP32) {
-      tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1);
+      tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
     } else {
-      tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1);
+      tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
     }
-    if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, 1);
+    if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, 1, sm.vel);
     __syncthreads();
     const float dt = sm.geo[kGeoDt], inv_tau = sm.geo[kGeoInvTau];
-    float gl[13];  // rx, sx, ry, sy and (nx, ny, Fscale) of the three faces
-#pragma unroll
-    for (int q = 0; q < 13; ++q) gl[q] = sm.geo[q];
-    int codes[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) codes[q] = sm.nbr[q];
 
+#pragma unroll
     for (int pass = 0; pass < NPASS; ++pass) {
       const int i = pass * kTcThreads + tid;
-      const float ex = __ldg(a.vel + kVelEx * QT + i), ey = __ldg(a.vel + kVelEy * QT + i);
-      const float w = __ldg(a.vel + kVelW * QT + i);
-      float rc[NP], fc[NP];
-#pragma unroll
-      for (int n = 0; n < NP; ++n) rc[n] = read_res ? __ldg(a.res + (k0 * NP + n) * QT + i) : 0.f;
+      const float ex = sm.vel[kVelEx * QT + i], ey = sm.vel[kVelEy * QT + i], w = __ldg(a.vel + kVelW * QT + i);
+      const float ar = ex * sm.geo[0] + ey * sm.geo[2], as = ex * sm.geo[1] + ey * sm.geo[3];
+      float fc[NP];
 #pragma unroll
       for (int m = 0; m < NP; ++m) fc[m] = sm.f[m * QT + i];
       {
         float flux[NF];
 #pragma unroll
         for (int fcx = 0; fcx < 3; ++fcx) {
-          const float en = ex * gl[4 + 3 * fcx] + ey * gl[5 + 3 * fcx];
-          const float c = 0.5f * (en - ab * fabsf(en)) * gl[6 + 3 * fcx];
-          const int code = codes[fcx];
+          const float en = ex * sm.geo[4 + 3 * fcx] + ey * sm.geo[5 + 3 * fcx];
+          const float c = 0.5f * (en - ab * fabsf(en)) * sm.geo[6 + 3 * fcx];
+          const int code = sm.nbr[fcx];
           if (code >= 0) {
-            const int64_t kn = code >> 3;
-            const int fn = (code >> 1) & 3;
 #pragma unroll
-            for (int aa = 0; aa < NFP; ++aa) {
-              const int a2 = (code & 1) ? NFP - 1 - aa : aa;
-              const int node = fn == 0 ? face_node(0, a2) : (fn == 1 ? face_node(1, a2) : face_node(2, a2));
-              flux[fcx * NFP + aa] = c * (fc[face_node(fcx, aa)] - __ldg(fin + (kn * NP + node) * QT + i));
-            }
+            for (int aa = 0; aa < NFP; ++aa)
+              flux[fcx * NFP + aa] = c * (fc[face_node(fcx, aa)] - tcur[fcx * NFP + aa]);
           } else {
             const int slot = -code - 1;  // wall slot: 4 * case + side
             const float fb = __ldg(a.wall_feq + slot * QT + i);
@@ -325,9 +346,10 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       }
       fence_proxy_async_smem();
       fence_before_sync();
-      __syncthreads();  // operand rows written (and, in the last pass, the state tile read)
+      __syncthreads();  // operand rows written (and, in the last pass, the tile read)
 
-      if (pass == NPASS - 1 && tile + gridDim.x < ntiles) {
+      const bool last = pass == NPASS - 1;
+      if (last && tile + gridDim.x < ntiles) {
         if (tid < 32) tc_issue_tile(a, sm, QT, tile + gridDim.x);
         pending = (j + 1) & 1;
       }
@@ -353,6 +375,11 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
         }
         mma_commit(bar_mma);
       }
+      // the next pass's (or next element's first pass's) loads fly during the MMAs
+      float rnext[NP], tnext[NF];
+      if (!last) fetch(k0, i + kTcThreads, rnext, tnext);
+      else if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x, tid, rnext, tnext);
+
       const bool mok = mbar_wait_bounded(bar_mma, mph, 2000000000ull);
       mph ^= 1u;
       if (__syncthreads_or(!mok)) {
@@ -362,23 +389,30 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       fence_after_sync();
 
       // ---- epilogue: rhs, collision, update; outputs straight from registers -------
-      {
-        float V[ND], W[ND], Lf[NL];
-        tmem_row<ND>(ta, V);
-        tmem_row<ND>(ta + ND, W);
-        tmem_row<NL>(ta + 2 * ND, Lf);
-        tmem_ld_wait();
-        const float ar = ex * gl[0] + ey * gl[2], as = ex * gl[1] + ey * gl[3];
 #pragma unroll
-        for (int n = 0; n < NP; ++n) {
-          float rhs = fmaf(-ar, V[n], fmaf(-as, W[n], Lf[n]));
-          rhs += collision<float>(sm.mom + n * 8, ex, ey, w, fc[n], inv_tau, third);
-          float r = dt * rhs;
-          if (read_res) r = fmaf(rkA, rc[n], r);
-          a.res[(k0 * NP + n) * QT + i] = r;
-          fout[(k0 * NP + n) * QT + i] = fmaf(rkB, r, fc[n]);
+      for (int c = 0; c < (NP + 7) / 8; ++c) {
+        float V[8], W[8], Lf[8];
+        tmem_ld8(ta + 8 * c, V);
+        tmem_ld8(ta + ND + 8 * c, W);
+        tmem_ld8(ta + 2 * ND + 8 * c, Lf);
+        tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int n = 8 * c + q;
+          if (n < NP) {
+            float rhs = fmaf(-ar, V[q], fmaf(-as, W[q], Lf[q]));
+            rhs += collision<float>(sm.mom + n * 8, ex, ey, w, fc[n], inv_tau, third);
+            float r = dt * rhs;
+            if (read_res) r = fmaf(rkA, rcur[n], r);
+            a.res[(k0 * NP + n) * QT + i] = r;
+            fout[(k0 * NP + n) * QT + i] = fmaf(rkB, r, fc[n]);
+          }
         }
       }
+#pragma unroll
+      for (int n = 0; n < NP; ++n) rcur[n] = rnext[n];
+#pragma unroll
+      for (int q = 0; q < NF; ++q) tcur[q] = tnext[q];
       fence_before_sync();
       __syncthreads();  // accumulators and operand rows are free for the next pass
     }
