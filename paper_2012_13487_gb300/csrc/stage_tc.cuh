@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
     __syncthreads();
     const float dt = sm.geo[kGeoDt], inv_tau = sm.geo[kGeoInvTau];
 
-#pragma unroll
+#pragma unroll 1
     for (int pass = 0; pass < NPASS; ++pass) {
       const int i = pass * kTcThreads + tid;
       const float ex = sm.vel[kVelEx * QT + i], ey = sm.vel[kVelEy * QT + i], w = __ldg(a.vel + kVelW * QT + i);
