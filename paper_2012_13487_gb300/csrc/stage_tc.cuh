@@ -255,7 +255,10 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   int64_t tile = blockIdx.x;
   if (tid < 32 && tile < ntiles) tc_issue_tile(a, sm, QT, tile);
 
-  const uint32_t sA_u = smem_u32(sA), sF_u = smem_u32(sF), sB_u = smem_u32(sB), sL_u = smem_u32(sL);
+  // matrix descriptors of the operand starts; a byte offset d inside an operand
+  // adds d >> 4 to the start-address field (all operands lie below 256 KB)
+  const uint64_t dA = sdesc(smem_u32(sA), 128, KCD * 128), dF = sdesc(smem_u32(sF), 128, KCL * 128);
+  const uint64_t dB = sdesc(smem_u32(sB), 128, KCD * 128), dL = sdesc(smem_u32(sL), 128, KCL * 128);
   constexpr uint32_t idD = idesc_tf32(128, 2 * ND), idL = idesc_tf32(128, NL);
   constexpr uint32_t aHalfD = kTcThreads * KD * 4, aHalfL = kTcThreads * KL * 4;  // hi -> lo bytes
   constexpr uint32_t bHalfD = 2 * ND * KD * 4, bHalfL = NL * KL * 4;
@@ -357,18 +360,18 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
         fence_after_sync();
 #pragma unroll
         for (int ks = 0; ks < KD / 8; ++ks) {
-          const uint32_t ko = uint32_t(ks * 256);
-          const uint64_t ah = sdesc(sA_u + ko, 128, KCD * 128), al = sdesc(sA_u + aHalfD + ko, 128, KCD * 128);
-          const uint64_t bh = sdesc(sB_u + ko, 128, KCD * 128), bl = sdesc(sB_u + bHalfD + ko, 128, KCD * 128);
+          const uint64_t ko = uint64_t(ks * 256) >> 4;
+          const uint64_t ah = dA + ko, al = dA + ((aHalfD >> 4) + ko);
+          const uint64_t bh = dB + ko, bl = dB + ((bHalfD >> 4) + ko);
           mma_tf32(tmem, ah, bh, idD, ks > 0);
           mma_tf32(tmem, al, bh, idD, 1);
           mma_tf32(tmem, ah, bl, idD, 1);
         }
 #pragma unroll
         for (int ks = 0; ks < KL / 8; ++ks) {
-          const uint32_t ko = uint32_t(ks * 256);
-          const uint64_t ah = sdesc(sF_u + ko, 128, KCL * 128), al = sdesc(sF_u + aHalfL + ko, 128, KCL * 128);
-          const uint64_t bh = sdesc(sL_u + ko, 128, KCL * 128), bl = sdesc(sL_u + bHalfL + ko, 128, KCL * 128);
+          const uint64_t ko = uint64_t(ks * 256) >> 4;
+          const uint64_t ah = dF + ko, al = dF + ((aHalfL >> 4) + ko);
+          const uint64_t bh = dL + ko, bl = dL + ((bHalfL >> 4) + ko);
           mma_tf32(tmem + 2 * ND, ah, bh, idL, ks > 0);
           mma_tf32(tmem + 2 * ND, al, bh, idL, 1);
           mma_tf32(tmem + 2 * ND, ah, bl, idL, 1);
