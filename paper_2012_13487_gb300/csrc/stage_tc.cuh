@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
 
   if (tid == 0) {
     mbar_init(bar_tile, 32);
-    mbar_init(bar_mma, 1);
+    mbar_init(bar_mma, 2);  // one commit from each of the two issuing threads
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
         if (tid < 32) tc_issue_tile(a, sm, QT, tile + gridDim.x);
         pending = (j + 1) & 1;
       }
+      // two threads in different warps issue the two products side by side
       if (tid == 0) {
         fence_after_sync();
 #pragma unroll
@@ -367,6 +368,9 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
           mma_tf32(tmem, al, bh, idD, 1);
           mma_tf32(tmem, ah, bl, idD, 1);
         }
+        mma_commit(bar_mma);
+      } else if (tid == 32) {
+        fence_after_sync();
 #pragma unroll
         for (int ks = 0; ks < KL / 8; ++ks) {
           const uint64_t ko = uint64_t(ks * 256) >> 4;
