@@ -371,7 +371,7 @@ cudaError_t launch_stage(const Group& g, int stage, int from, cudaStream_t st) {
   }
   StageArgs<float> a;
   fill_stage_args(g, stage, from, a);
-  if (g.tc) return e.launch_tc(&a, g.grid, g.smem, st);
+  if (g.tc) return e.launch_tc(g.store, &a, g.grid, g.smem, st);
   return e.launch(g.store, &a, g.grid, g.tpb, g.smem, st);
 }
 
@@ -399,8 +399,8 @@ int configure_tc(Batch& b, Group& g) {
   // than its tensor memory serves
   const int max_ctas = 512 / e.tc_tmem_cols(g.Qp);
   smem = std::max(smem, size_t(smem_sm) / size_t(max_ctas + 1) + 1024);
-  FEDBM_CK(e.set_smem_tc(g.Qp, smem));
-  const int per_sm = e.occupancy_tc(g.Qp, smem);
+  FEDBM_CK(e.set_smem_tc(g.store, g.Qp, smem));
+  const int per_sm = e.occupancy_tc(g.store, g.Qp, smem);
   const int by_smem = int(size_t(smem_sm) / smem);
   if (per_sm < 1 || std::max(per_sm, by_smem) * e.tc_tmem_cols(g.Qp) > 512)
     return fail(FEDBM_EINVAL, "tensor-core stage kernel cannot be resident within tensor memory");
@@ -812,7 +812,12 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
          for (Group& g : b->groups) {
            const int epc = g.epc, tpb = g.tpb, st = g.nstages;
            if ((r = build_group(*b, g)) != FEDBM_OK) return r;
-           const bool want_tc = g.tc_mode > 0 || (g.tc_mode == 0 && epc == 0 && tpb == 0 && st == 0 && tc_available(g));
+           // default: tensor cores for FP32 and BF16 state up to 256 padded
+           // velocities (measured no slower than the FMA kernel there); the
+           // FP16 form's rescaling sweep and the eight dependent MMA rounds
+           // of 1024 velocities make the FMA kernel the faster one
+           const bool want_tc = g.tc_mode > 0 || (g.tc_mode == 0 && epc == 0 && tpb == 0 && st == 0 &&
+                                                   g.store != kStoreF16 && g.Qp <= 256 && tc_available(g));
            if (want_tc) {
              if ((r = configure_tc(*b, g)) != FEDBM_OK) return r;
            } else if ((r = configure_tiles(*b, g, epc, tpb, st)) != FEDBM_OK) {

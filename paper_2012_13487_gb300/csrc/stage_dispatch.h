@@ -11,12 +11,13 @@ struct StageEntry {
   cudaError_t (*set_smem)(int store_kind, int Qp, size_t smem);
   cudaError_t (*upload)(const double* Dr, const double* Ds, const double* LIFT);
   int (*occupancy)(int store_kind, int Qp, int block, size_t smem);  // resident CTAs per SM
-  // tensor-core form (FP32 state, 128, 256 or 1024 velocities, one element per CTA)
+  // tensor-core form (FP32, BF16 or FP16 state; 128, 256 or 1024 velocities;
+  // one element per CTA)
   size_t (*tc_smem)(int store_kind, int Qp);  // dynamic shared memory; 0 = no such form
   int (*tc_tmem_cols)(int Qp);                 // tensor-memory columns per CTA
-  cudaError_t (*launch_tc)(const void* args, int grid, size_t smem, cudaStream_t st);
-  cudaError_t (*set_smem_tc)(int Qp, size_t smem);
-  int (*occupancy_tc)(int Qp, size_t smem);
+  cudaError_t (*launch_tc)(int store_kind, const void* args, int grid, size_t smem, cudaStream_t st);
+  cudaError_t (*set_smem_tc)(int store_kind, int Qp, size_t smem);
+  int (*occupancy_tc)(int store_kind, int Qp, size_t smem);
 };
 
 StageEntry stage_entry_p0();

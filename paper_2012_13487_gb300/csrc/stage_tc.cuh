@@ -1,5 +1,6 @@
-// Tensor-core form of the stage kernel (FP32 state, QT = 128, 256 or 1024
-// velocities, 128 threads, one velocity per thread in each 128-velocity pass).  Included by stage_impl.cuh inside its namespace:
+// Tensor-core form of the stage kernel (FP32 state or BF16/FP16 deviation state
+// with FP32 arithmetic; QT = 128, 256 or 1024 velocities; 128 threads, one
+// velocity per thread in each 128-velocity pass).  Included by stage_impl.cuh inside its namespace:
 // it reuses the tile loads, node moments, wall numerators and collision term of
 // the FMA kernel and replaces the element-local contractions of phase 4,
 //   V = (f - f_0 1) Dr^T,  W = (f - f_0 1) Ds^T,  Lf = flux LIFT^T,
@@ -39,17 +40,18 @@ __host__ __device__ constexpr int kidx(int r, int k, int KC) {
 // Shared-memory layout (byte offsets) of one CTA.  Only the element's state
 // tile comes through shared memory (the node moments are reductions over all
 // velocities); each thread loads its own residual and neighbour-trace columns
-// into registers and writes its outputs from registers.
+// into registers and writes its outputs from registers.  s_bytes is the state
+// element size; the velocity rows are e_x, e_y (and w for the deviation forms).
 struct Layout {
-  size_t bar, f, A, F, B, L, geo, nbr, mom, wn, vel, end;
+  size_t bar, f, A, F, B, L, geo, nbr, sc, mom, wn, vel, end;
 };
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
-__host__ __device__ inline Layout layout(int QT) {
+__host__ __device__ inline Layout layout(int QT, int s_bytes, int vel_rows) {
   Layout o;
   size_t b = 0;
   o.bar = b;  b += 32;                                       // tile barrier, MMA barrier, TMEM address
   b = al(b, 128);
-  o.f = b;    b += size_t(NP) * QT * 4;                       // element state tile
+  o.f = b;    b += size_t(NP) * QT * s_bytes;                 // element state tile
   b = al(b, 128);
   o.A = b;    b += 2 * size_t(kTcThreads) * KD * 4;           // (f - f_0) hi|lo of one pass
   o.F = b;    b += 2 * size_t(kTcThreads) * KL * 4;           // face fluxes hi|lo of one pass
@@ -57,9 +59,10 @@ __host__ __device__ inline Layout layout(int QT) {
   o.L = b;    b += 2 * size_t(NL) * KL * 4;                   // LIFT hi|lo
   o.geo = b;  b += al(kGeoStrideDev * 4, 16);
   o.nbr = b;  b += 16;
+  o.sc = b;   b += 16;                                        // element scale, new scale, max deviation
   o.mom = b;  b += al(size_t(NP) * 8 * 4, 16);
   o.wn = b;   b += al(size_t(NF) * 4, 16);
-  o.vel = b;  b += al(size_t(2) * QT * 4, 16);              // e_x, e_y rows (the FP32 paths read no w row)
+  o.vel = b;  b += al(size_t(vel_rows) * QT * 4, 16);
   o.end = b;
   return o;
 }
@@ -156,19 +159,33 @@ __device__ __forceinline__ void put_row(float* hi, float* lo, int r, const float
   }
 }
 
+// deviation form whose 16-bit format has FP32's exponent range (BF16)
+template <class ST>
+__host__ __device__ constexpr bool keeps_scale() {
+  if constexpr (ST::dev) return ST::qmax_log2 == 0;
+  else return false;
+}
+
 }  // namespace tc
 
 // Bulk copies of one element's state tile and geometry (warp 0); the lanes
-// also store its three face codes.  Every lane arrives on the barrier, so the
-// plain stores are visible to the threads that wait on it.
-__device__ __forceinline__ void tc_issue_tile(const StageArgs<float>& a, StageSmem<float, float>& sm, int QT,
-                                              int64_t k0) {
+// also store its three face codes (and, for the deviation forms, its scale and
+// a zero running maximum).  Every lane arrives on the barrier, so the plain
+// stores are visible to the threads that wait on it.
+template <class ST>
+__device__ __forceinline__ void tc_issue_tile(const StageArgs<float>& a, StageSmem<float, typename ST::S>& sm,
+                                              int QT, int64_t k0) {
+  using S = typename ST::S;
   const int lane = threadIdx.x & 31;
   if (lane < 3) sm.nbr[lane] = __ldg(a.nbr + k0 * 3 + lane);
-  const uint32_t tile_bytes = uint32_t(NP * QT * 4), geo_bytes = uint32_t(kGeoStrideDev * 4);
+  if constexpr (ST::dev) {
+    if (lane == 3) sm.scale[0] = __ldg(a.scale_in + k0);
+    if (lane == 4) sm.dmax[0] = 0u;
+  }
+  const uint32_t tile_bytes = uint32_t(NP * QT * sizeof(S)), geo_bytes = uint32_t(kGeoStrideDev * 4);
   mbar_arrive_expect_tx(sm.bar, lane == 0 ? tile_bytes + geo_bytes + a.extra_tx : 0u);
   if (lane == 0) {
-    bulk_load(sm.f, static_cast<const float*>(a.f_in) + k0 * NP * QT, tile_bytes, sm.bar);
+    bulk_load(sm.f, static_cast<const S*>(a.f_in) + k0 * NP * QT, tile_bytes, sm.bar);
     bulk_load(sm.geo, a.geo + k0 * kGeoStrideDev, geo_bytes, sm.bar);
   }
 }
@@ -181,14 +198,22 @@ __device__ __forceinline__ void tc_issue_tile(const StageArgs<float>& a, StageSm
 // MMAs, and the epilogue reads the accumulators and writes the new state and
 // residual from registers.  Once the last pass has read the state tile, the
 // next element's copy starts and overlaps that pass's MMAs and epilogue.
-template <int QT>
+template <class ST, int QT>
 __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const StageArgs<float> a) {
-  using ST = StoreF32;
+  using S = typename ST::S;
   using namespace tc;
+  constexpr int VROWS = ST::dev ? 3 : 2;
+  // BF16 keeps FP32's exponent range: a power-of-two element scale changes
+  // neither the rounding of q nor the decoded f = w (1 + s q), so the element
+  // keeps its scale and the new state is encoded straight from registers.
+  // FP16 (|q| < 2^15) needs the new scale of the element's largest deviation,
+  // found after every velocity is done, and a second encoding sweep.
+  constexpr bool kKeepScale = tc::keeps_scale<ST>();
+  constexpr bool kRescale = ST::dev && !kKeepScale;
   static_assert(QT % kTcThreads == 0, "whole 128-velocity passes");
   constexpr int NPASS = QT / kTcThreads;
   extern __shared__ __align__(128) unsigned char smem[];  // operands need 16-byte alignment
-  const Layout o = layout(QT);
+  const Layout o = layout(QT, int(sizeof(S)), VROWS);
   uint64_t* bar_tile = reinterpret_cast<uint64_t*>(smem + o.bar);
   uint64_t* bar_mma = bar_tile + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + o.bar + 16);
@@ -196,16 +221,16 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   float* sF = reinterpret_cast<float*>(smem + o.F);
   float* sB = reinterpret_cast<float*>(smem + o.B);
   float* sL = reinterpret_cast<float*>(smem + o.L);
-  StageSmem<float, float> sm;
+  StageSmem<float, S> sm;
   sm.bar = bar_tile;
-  sm.f = reinterpret_cast<float*>(smem + o.f);
+  sm.f = reinterpret_cast<S*>(smem + o.f);
   sm.res = nullptr;
   sm.tr = nullptr;
   sm.geo = reinterpret_cast<float*>(smem + o.geo);
   sm.nbr = reinterpret_cast<int*>(smem + o.nbr);
-  sm.scale = nullptr;
-  sm.nscale = nullptr;
-  sm.dmax = nullptr;
+  sm.scale = reinterpret_cast<float*>(smem + o.sc);       // element scale (deviation forms)
+  sm.nscale = sm.scale + 1;                                // its new scale
+  sm.dmax = reinterpret_cast<unsigned*>(sm.scale + 2);     // max |f_new/w - 1| as float bits
   sm.mom = reinterpret_cast<float*>(smem + o.mom);
   sm.wn = reinterpret_cast<float*>(smem + o.wn);
   sm.vel = reinterpret_cast<float*>(smem + o.vel);
@@ -215,8 +240,8 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   const bool read_res = rkA != 0.f;
   const bool third = a.eq_order == 3;
   const int64_t ntiles = a.K;  // one element per tile
-  const float* fin = static_cast<const float*>(a.f_in);
-  float* fout = static_cast<float*>(a.f_out);
+  const S* fin = static_cast<const S*>(a.f_in);
+  S* fout = static_cast<S*>(a.f_out);
 
   if (tid == 0) {
     mbar_init(bar_tile, 32);
@@ -228,7 +253,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
                  "n"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  for (int v = tid; v < 2 * QT; v += kTcThreads) sm.vel[v] = a.vel[v];
+  for (int v = tid; v < VROWS * QT; v += kTcThreads) sm.vel[v] = a.vel[v];
   // B operands from the FP64 operators: [Dr; Ds] (rows n, then ND + n) and LIFT
   for (int v = tid; v < 2 * ND * KD; v += kTcThreads) {
     const int n = v / KD, m = v % KD;
@@ -253,7 +278,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   const uint32_t tmem = *tslot;
 
   int64_t tile = blockIdx.x;
-  if (tid < 32 && tile < ntiles) tc_issue_tile(a, sm, QT, tile);
+  if (tid < 32 && tile < ntiles) tc_issue_tile<ST>(a, sm, QT, tile);
 
   // matrix descriptors of the operand starts; a byte offset d inside an operand
   // adds d >> 4 to the start-address field (all operands lie below 256 KB)
@@ -269,16 +294,18 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   auto fetch = [&](int64_t k, int i, float (&rx)[NP], float (&tx)[NF]) {
 #pragma unroll
     for (int n = 0; n < NP; ++n) rx[n] = read_res ? __ldg(a.res + (k * NP + n) * QT + i) : 0.f;
+    const float wi = ST::dev ? __ldg(a.vel + kVelW * QT + i) : 0.f;
 #pragma unroll
     for (int fcx = 0; fcx < 3; ++fcx) {
       const int code = __ldg(a.nbr + k * 3 + fcx);
       const int64_t kn = code >= 0 ? int64_t(code >> 3) : k;  // walls: an in-bounds address, not used
       const int fn = (code >> 1) & 3;
+      const float wsn = ST::dev ? wi * __ldg(a.scale_in + kn) : 0.f;
 #pragma unroll
       for (int aa = 0; aa < NFP; ++aa) {
         const int a2 = (code & 1) ? NFP - 1 - aa : aa;
         const int node = fn == 0 ? face_node(0, a2) : (fn == 1 ? face_node(1, a2) : face_node(2, a2));
-        tx[fcx * NFP + aa] = code >= 0 ? __ldg(fin + (kn * NP + node) * QT + i) : 0.f;
+        tx[fcx * NFP + aa] = code >= 0 ? decode<ST>(fin[(kn * NP + node) * QT + i], wi, wsn) : 0.f;
       }
     }
   };
@@ -310,15 +337,20 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
     if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, 1, sm.vel);
     __syncthreads();
     const float dt = sm.geo[kGeoDt], inv_tau = sm.geo[kGeoInvTau];
+    const float s_el = ST::dev ? sm.scale[0] : 0.f;
+    const float inv_s_el = ST::dev ? 1.0f / s_el : 0.f;
+    if (kKeepScale && tid == 0) a.scale_out[k0] = s_el;
+    float dloc = 0.f;  // FP16 form: this thread's max |f_new/w - 1|
 
 #pragma unroll 1
     for (int pass = 0; pass < NPASS; ++pass) {
       const int i = pass * kTcThreads + tid;
       const float ex = sm.vel[kVelEx * QT + i], ey = sm.vel[kVelEy * QT + i], w = __ldg(a.vel + kVelW * QT + i);
+      const float invw = ST::dev ? __ldg(a.vel + kVelInvW * QT + i) : 0.f;
       const float ar = ex * sm.geo[0] + ey * sm.geo[2], as = ex * sm.geo[1] + ey * sm.geo[3];
       float fc[NP];
 #pragma unroll
-      for (int m = 0; m < NP; ++m) fc[m] = sm.f[m * QT + i];
+      for (int m = 0; m < NP; ++m) fc[m] = decode<ST>(sm.f[m * QT + i], w, w * s_el);
       {
         float flux[NF];
 #pragma unroll
@@ -352,8 +384,8 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       __syncthreads();  // operand rows written (and, in the last pass, the tile read)
 
       const bool last = pass == NPASS - 1;
-      if (last && tile + gridDim.x < ntiles) {
-        if (tid < 32) tc_issue_tile(a, sm, QT, tile + gridDim.x);
+      if (!kRescale && last && tile + gridDim.x < ntiles) {
+        if (tid < 32) tc_issue_tile<ST>(a, sm, QT, tile + gridDim.x);
         pending = (j + 1) & 1;
       }
       // two threads in different warps issue the two products side by side
@@ -412,7 +444,14 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
             float r = dt * rhs;
             if (read_res) r = fmaf(rkA, rcur[n], r);
             a.res[(k0 * NP + n) * QT + i] = r;
-            fout[(k0 * NP + n) * QT + i] = fmaf(rkB, r, fc[n]);
+            const float fnew = new_f<ST>(fc[n], rkB, r);
+            if constexpr (kRescale) {
+              dloc = fmaxf(dloc, fabsf((fnew - w) * invw));
+            } else if constexpr (kKeepScale) {
+              fout[(k0 * NP + n) * QT + i] = ST::from_r((fnew - w) * invw * inv_s_el);
+            } else {
+              fout[(k0 * NP + n) * QT + i] = fnew;
+            }
           }
         }
       }
@@ -424,6 +463,42 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       __syncthreads();  // accumulators and operand rows are free for the next pass
     }
     if (failed) break;
+
+    // ---- FP16 form: new element scale, then encode from the old tile -----------
+    if constexpr (kRescale) {
+      atomicMax(sm.dmax, __float_as_uint(dloc));
+      __syncthreads();
+      if (tid == 0) {
+        const float md = __uint_as_float(sm.dmax[0]);
+        float sc = 1.0f;
+        if (md > 0.f) {
+          int ex2;
+          frexpf(md, &ex2);
+          sc = ldexpf(1.0f, ex2 - ST::qmax_log2);
+        }
+        sm.nscale[0] = sc;
+        a.scale_out[k0] = sc;
+      }
+      __syncthreads();
+      const float inv_s = 1.0f / sm.nscale[0];
+#pragma unroll 1
+      for (int pass = 0; pass < NPASS; ++pass) {
+        const int i = pass * kTcThreads + tid;
+        const float w = sm.vel[kVelW * QT + i], invw = __ldg(a.vel + kVelInvW * QT + i);
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          // the residual this thread stored above, and the same f_new as there
+          const float fold = decode<ST>(sm.f[n * QT + i], w, w * s_el);
+          const float fnew = new_f<ST>(fold, rkB, a.res[(k0 * NP + n) * QT + i]);
+          fout[(k0 * NP + n) * QT + i] = ST::from_r((fnew - w) * invw * inv_s);
+        }
+      }
+      __syncthreads();  // the state tile, scale and maximum are free for the next element
+      if (tile + gridDim.x < ntiles) {
+        if (tid < 32) tc_issue_tile<ST>(a, sm, QT, tile + gridDim.x);
+        pending = (j + 1) & 1;
+      }
+    }
   }
   if (failed) {
     if (tid == 0 && a.err) atomicExch(a.err, 1);
@@ -443,37 +518,44 @@ constexpr int kTcMaxP = 4;
 
 // Dynamic shared memory of the tensor-core kernel (0 = no tensor-core form).
 size_t tc_smem(int store_kind, int Qp) {
-  if (P > kTcMaxP || store_kind != kStoreF32 || (Qp != 128 && Qp != 256 && Qp != 1024)) return 0;
-  return tc::layout(Qp).end;
+  if (P > kTcMaxP || store_kind == kStoreF64 || (Qp != 128 && Qp != 256 && Qp != 1024)) return 0;
+  const bool dev = store_kind != kStoreF32;
+  return tc::layout(Qp, dev ? 2 : 4, dev ? 3 : 2).end;
 }
 
 // Tensor-memory columns one CTA of the tensor-core kernel allocates.
 int tc_tmem_cols(int) { return tc::kTcCols; }
 
-cudaError_t launch_tc(const void* args, int grid, size_t smem, cudaStream_t st) {
-  if constexpr (P <= kTcMaxP) {
-    const auto& a = *static_cast<const StageArgs<float>*>(args);
-    if (a.Qp == 256) stage_kernel_tc<256><<<grid, tc::kTcThreads, smem, st>>>(a);
-    else if (a.Qp == 128) stage_kernel_tc<128><<<grid, tc::kTcThreads, smem, st>>>(a);
-    else if (a.Qp == 1024) stage_kernel_tc<1024><<<grid, tc::kTcThreads, smem, st>>>(a);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
-  }
-  return cudaErrorInvalidValue;
-}
-
+// Calls fn with the tensor-core kernel of a store kind and velocity count.
 template <class Fn>
-cudaError_t with_tc_kernel(int Qp, Fn fn) {
+cudaError_t with_tc_kernel(int store_kind, int Qp, Fn fn) {
   if constexpr (P <= kTcMaxP) {
-    if (Qp == 256) return fn(stage_kernel_tc<256>);
-    if (Qp == 128) return fn(stage_kernel_tc<128>);
-    if (Qp == 1024) return fn(stage_kernel_tc<1024>);
+    auto by_q = [&](auto st) -> cudaError_t {
+      using ST = decltype(st);
+      if (Qp == 256) return fn(stage_kernel_tc<ST, 256>);
+      if (Qp == 128) return fn(stage_kernel_tc<ST, 128>);
+      if (Qp == 1024) return fn(stage_kernel_tc<ST, 1024>);
+      return cudaErrorInvalidValue;
+    };
+    if (store_kind == kStoreF32) return by_q(StoreF32{});
+    if (store_kind == kStoreBF16) return by_q(StoreBF16{});
+    if (store_kind == kStoreF16) return by_q(StoreF16{});
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t set_smem_tc(int Qp, size_t smem) {
-  return with_tc_kernel(Qp, [smem](auto kernel) {
+cudaError_t launch_tc(int store_kind, const void* args, int grid, size_t smem, cudaStream_t st) {
+  const auto& a = *static_cast<const StageArgs<float>*>(args);
+  cudaError_t e = with_tc_kernel(store_kind, a.Qp, [&](auto kernel) {
+    kernel<<<grid, tc::kTcThreads, smem, st>>>(a);
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t set_smem_tc(int store_kind, int Qp, size_t smem) {
+  return with_tc_kernel(store_kind, Qp, [smem](auto kernel) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     // all of the SM's unified L1/shared storage as shared memory, so that
@@ -484,9 +566,11 @@ cudaError_t set_smem_tc(int Qp, size_t smem) {
 
 // Resident CTAs per SM from the kernel's registers, its shared memory (with
 // the per-block reservation) and the thread limit.
-int occupancy_tc(int Qp, size_t smem) {
+int occupancy_tc(int store_kind, int Qp, size_t smem) {
   cudaFuncAttributes fa;
-  if (with_tc_kernel(Qp, [&fa](auto kernel) { return cudaFuncGetAttributes(&fa, kernel); }) != cudaSuccess) return 0;
+  if (with_tc_kernel(store_kind, Qp, [&fa](auto kernel) { return cudaFuncGetAttributes(&fa, kernel); }) !=
+      cudaSuccess)
+    return 0;
   int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, reserved = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);

@@ -1,7 +1,7 @@
 """Tensor-core form of the stage kernel (tcgen05 TF32 MMAs with a hi/lo split
 for the Dr, Ds and LIFT contractions) against the FP64 oracle and against the
-FMA form, on the shapes it serves: FP32 state, 128, 256 or 1024 padded
-velocities, degree <= 4."""
+FMA form, on the shapes it serves: FP32 state or BF16/FP16 deviation state,
+128, 256 or 1024 padded velocities, degree <= 4."""
 import numpy as np
 import pytest
 
@@ -58,10 +58,13 @@ def test_tc_1024_velocities_cavity_kn8(p):
 def test_tc_default_selection_and_rejection():
     from paper_2012_13487_gb300 import fedbm as fb
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32").info.tensor_cores == 1
-    # explicit FMA tiles, other velocity counts, 16-bit state, degree 5: FMA form
+    # explicit FMA tiles, other velocity counts, FP64 state, degree 5: FMA form
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32", epc=2).info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("gh", 4)), "fp32").info.tensor_cores == 0
-    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "bf16").info.tensor_cores == 0
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "bf16").info.tensor_cores == 1
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp64").info.tensor_cores == 0
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp16").info.tensor_cores == 0
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp16", tc=1).info.tensor_cores == 1
     assert cases.solver(cases.cavity(3, 3, 5, velset=("nc", 16)), "fp32").info.tensor_cores == 0
     with pytest.raises(fb.FedbmError) as e:
         cases.solver(cases.cavity(3, 3, 4, velset=("gh", 4)), "fp32", tc=1)
@@ -129,3 +132,29 @@ def test_tc_batch_groups_toggle_bitwise_with_single_solvers():
     assert b.info(0).tensor_cores == 0
     fb.fedbm_batch_set_tensor_cores(b.h, g, 1)
     assert b.info(0).tensor_cores == 1
+
+
+@pytest.mark.parametrize("prec,u", [("bf16", 2.0 ** -8), ("fp16", 2.0 ** -11)])
+@pytest.mark.parametrize("p,vs", [(4, ("nc", 16)), (3, ("nc", 32))])
+def test_tc_deviation_forms(prec, u, p, vs):
+    """16-bit deviation state on the tensor-core form: after 2 steps every value
+    is within the storage bound of the 16-bit parity tests of the oracle
+    (12 encodings' worth of u relative to w times the element's largest
+    deviation), and the tensor-core and FMA forms agree to that bound too."""
+    c = cases.cavity(4, 3, p, velset=vs, kn=8.0)
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=1e-2, seed=41)
+    out = {}
+    for tc in (1, -1):
+        s = cases.solver(c, prec, "fp64", tc=tc)
+        assert s.info.tensor_cores == (1 if tc == 1 else 0)
+        s.set_state(f0)
+        s.step(2)
+        out[tc] = s.state()
+        s.mass()
+    f1 = pr.run(f0, 2)
+    w = pr.w[None, None, :]
+    md = np.abs(f1 / w - 1.0).max(axis=(1, 2))[:, None, None]
+    for tc in (1, -1):
+        assert (np.abs(out[tc] - f1) / (w * md)).max() < 12 * u
+    assert (np.abs(out[1] - out[-1]) / (w * md)).max() < 12 * u
