@@ -742,13 +742,22 @@ cudaError_t launch_one(const void* args, int grid, int block, size_t smem, cudaS
 }
 
 // Velocity counts with a specialised kernel (the GH D2Q16 and NC 16x16 /
-// 32x32 sets); other counts use the runtime-stride kernel.
+// 32x32 sets; the larger sets only at the degrees their workloads use, which
+// keeps the high-degree translation units quick to compile); other counts use
+// the runtime-stride kernel.
+constexpr bool specialised_q(int Qp) {
+  return (Qp == 16 && P <= 5) || (Qp == 256 && P <= 5) || (Qp == 1024 && P <= 4);
+}
+
 template <class ST>
 cudaError_t launch_q(int Qp, const void* args, int grid, int block, size_t smem, cudaStream_t st) {
   if constexpr (ST::kind != kStoreF64) {
-    if (Qp == 16) return launch_one<ST, 16>(args, grid, block, smem, st);
-    if (Qp == 256) return launch_one<ST, 256>(args, grid, block, smem, st);
-    if (Qp == 1024) return launch_one<ST, 1024>(args, grid, block, smem, st);
+    if constexpr (specialised_q(16))
+      if (Qp == 16) return launch_one<ST, 16>(args, grid, block, smem, st);
+    if constexpr (specialised_q(256))
+      if (Qp == 256) return launch_one<ST, 256>(args, grid, block, smem, st);
+    if constexpr (specialised_q(1024))
+      if (Qp == 1024) return launch_one<ST, 1024>(args, grid, block, smem, st);
   }
   return launch_one<ST, 0>(args, grid, block, smem, st);
 }
@@ -758,9 +767,12 @@ int occupancy_q(int Qp, int block, size_t smem) {
   int n = 0;
   auto occ = [&](auto kernel) { cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem); };
   if constexpr (ST::kind != kStoreF64) {
-    if (Qp == 16) { occ(stage_kernel<ST, 16>); return n; }
-    if (Qp == 256) { occ(stage_kernel<ST, 256>); return n; }
-    if (Qp == 1024) { occ(stage_kernel<ST, 1024>); return n; }
+    if constexpr (specialised_q(16))
+      if (Qp == 16) { occ(stage_kernel<ST, 16>); return n; }
+    if constexpr (specialised_q(256))
+      if (Qp == 256) { occ(stage_kernel<ST, 256>); return n; }
+    if constexpr (specialised_q(1024))
+      if (Qp == 1024) { occ(stage_kernel<ST, 1024>); return n; }
   }
   occ(stage_kernel<ST, 0>);
   return n;
@@ -783,9 +795,12 @@ cudaError_t set_smem_q(int Qp, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   };
   if constexpr (ST::kind != kStoreF64) {
-    if (Qp == 16) return set(stage_kernel<ST, 16>);
-    if (Qp == 256) return set(stage_kernel<ST, 256>);
-    if (Qp == 1024) return set(stage_kernel<ST, 1024>);
+    if constexpr (specialised_q(16))
+      if (Qp == 16) return set(stage_kernel<ST, 16>);
+    if constexpr (specialised_q(256))
+      if (Qp == 256) return set(stage_kernel<ST, 256>);
+    if constexpr (specialised_q(1024))
+      if (Qp == 1024) return set(stage_kernel<ST, 1024>);
   }
   return set(stage_kernel<ST, 0>);
 }
