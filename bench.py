@@ -291,6 +291,23 @@ def oracle_sample(w, seconds, nelem=512, min_stages=1, max_stages=10 ** 9):
 
 
 # ---------------------------------------------------------------- arms
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (a job's time is its slowest rank's); x
+    itself on one rank (dist None).  device: "cuda" for NCCL, "cpu" for gloo."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job units per second: every rank (a replica) processes
+    units_per_rank in the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -366,12 +383,9 @@ def run_ours(args, w, name):
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
     mass = s.mass()   # also raises on NaN / rho <= 0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     secs = ms / 1e3
-    value = world * dof * 5 * args.steps / secs
+    value = job_throughput(world, dof * 5 * args.steps, secs)
 
     # roofline of the stage kernel: algorithmic bytes / average launch time
     alg_bytes_step = dof * algorithmic_bytes_per_dof_step(w["precision"])
@@ -400,12 +414,8 @@ def run_ours(args, w, name):
         fb.fedbm_rk_step(s.h, 1)
         fb.fedbm_get_moments(s.h, rho, ux, uy, False)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * dof * 5 * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_throughput(world, dof * 5 * e2e_steps, e2e_s)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -477,12 +487,8 @@ def run_batch_workload(args, w, name, st, world, rank, dist):
         dist.barrier()
     bat = measure_batch(w, st, args.steps, args.warmup, max(1, min(args.steps, 3)), not args.no_tune)
     clocks = sampler.stop()
-    ms = bat["ms_per_step"] * args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * bat["dof"] * 5 * args.steps / (ms / 1e3)
+    ms = max_over_ranks(bat["ms_per_step"] * args.steps, dist, "cuda")
+    value = job_throughput(world, bat["dof"] * 5 * args.steps, ms / 1e3)
     peak, peak_kind = hbm_peak()
     achieved = bat["dof"] * algorithmic_bytes_per_dof_step("fp32") * args.steps / (ms / 1e3) / 1e9
     if rank == 0:
