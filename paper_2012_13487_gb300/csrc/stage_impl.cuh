@@ -133,7 +133,7 @@ struct AccN {
   __device__ float value() const { return s + c; }
 };
 
-__device__ __forceinline__ int pow2_floor_32(int g) {
+__host__ __device__ constexpr int pow2_floor_32(int g) {
   return g >= 32 ? 32 : g >= 16 ? 16 : g >= 8 ? 8 : g >= 4 ? 4 : g >= 2 ? 2 : 1;
 }
 
@@ -211,17 +211,27 @@ struct Vec16 {
 
 // Phase 2: rho, u_x, u_y of every node of the tile into s_mom.  G lanes share a
 // node; each lane reduces 16-byte chunks of the node's velocity row.
-template <class ST, class Acc, int QT>
+// Lanes per node group: the largest power of two <= 32 that gives every node
+// of the tile a group and no lane more than one chunk fewer than another.
+__host__ __device__ constexpr int moment_lanes(int nth, int epc, int nchunk) {
+  int G = pow2_floor_32(nth / (epc * NP));
+  while (G > 1 && G > nchunk) G >>= 1;
+  return G;
+}
+
+// NTH > 0: a CTA of NTH threads and one element per tile (the tensor-core
+// kernel), so the lane grouping and the chunk loop are compile-time.
+template <class ST, class Acc, int QT, int NTH = 0>
 __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename ST::S* s_f,
                              const float* s_scale, const typename ST::R* s_geo, typename ST::R* s_mom, int ne,
                              const typename ST::R* s_vel) {
   using R = typename ST::R;
   using S = typename ST::S;
   constexpr int V = Vec16<ST>::N;
-  const int Qp = QT > 0 ? QT : a.Qp, tid = threadIdx.x, nth = blockDim.x;
+  static_assert(NTH == 0 || QT > 0, "a compile-time CTA needs a compile-time velocity count");
+  const int Qp = QT > 0 ? QT : a.Qp, tid = threadIdx.x, nth = NTH > 0 ? NTH : blockDim.x;
   const int nchunk = Qp / V;
-  int G = pow2_floor_32(nth / (a.epc * NP));
-  while (G > 1 && G > nchunk) G >>= 1;
+  const int G = NTH > 0 ? moment_lanes(NTH, 1, (QT > 0 ? QT : 1) / V) : moment_lanes(nth, a.epc, nchunk);
   const int ngroups = nth / G, grp = tid / G, lane = tid % G;
   const int npair = ne * NP;
   const R* ex = s_vel + kVelEx * Qp;  // shared-memory copy of the velocity rows
@@ -233,7 +243,7 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
     Acc m0, m1, m2;
     if (valid) {
       const S* row = s_f + size_t(pair) * Qp;
-      for (int c = lane; c < nchunk; c += G) {
+      auto chunk = [&](int c) {
         __align__(16) S v[V];
         __align__(16) R exv[V], eyv[V], wvv[V];
         *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(row + c * V);
@@ -258,6 +268,13 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
         m0.add(c0);
         m1.add(c1);
         m2.add(c2);
+      };
+      if constexpr (NTH > 0) {
+        constexpr int GC = moment_lanes(NTH > 0 ? NTH : 1, 1, (QT > 0 ? QT : V) / V);
+#pragma unroll
+        for (int c = 0; c < (QT > 0 ? QT : V) / V; c += GC) chunk(c + lane);
+      } else {
+        for (int c = lane; c < nchunk; c += G) chunk(c);
       }
     }
     m0.reduce(G);

@@ -328,11 +328,11 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
     if (!a.collision) {
       for (int v = tid; v < NP * 8; v += kTcThreads) sm.mom[v] = 0.f;
     } else if (a.red == kRedFP64) {
-      tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
+      tile_moments<ST, AccD, QT, kTcThreads>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
     } else if (a.red == kRedCompFP32) {
-      tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
+      tile_moments<ST, AccN, QT, kTcThreads>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
     } else {
-      tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
+      tile_moments<ST, AccF, QT, kTcThreads>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
     }
     if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, 1, sm.vel);
     __syncthreads();
