@@ -186,46 +186,81 @@ __global__ void decode_residual_kernel(const R* in, double* out, int64_t K, int 
   }
 }
 
-// node moments in FP64 (one thread per node)
+// One value of a node row in the state's compute precision R (FP64 state:
+// double; FP32 and 16-bit states: float, f = w + (w s) q for the latter).
 template <class ST>
-__global__ void moments_kernel(const void* in, const float* scale, const double* vel64, int64_t K, int Np,
+__device__ __forceinline__ typename ST::R decode_r(const typename ST::S v, typename ST::R w, typename ST::R ws) {
+  if constexpr (ST::dev) return fmaf(ws, ST::to_r(v), w);
+  else return typename ST::R(v);
+}
+
+// Sums over one node row: one warp per node, lanes on consecutive velocities
+// (coalesced), per-lane partial sums in R, the warp reduction in FP64.
+template <class ST>
+__device__ __forceinline__ void node_sums(const typename ST::S* row, const typename ST::R* vel, int Qp,
+                                          typename ST::R s, int lane, double& d0, double& d1, double& d2) {
+  using R = typename ST::R;
+  R m0 = 0, m1 = 0, m2 = 0;
+  for (int i = lane; i < Qp; i += 32) {
+    const R w = vel[kVelW * Qp + i];
+    const R f = decode_r<ST>(row[i], w, w * s);
+    m0 += f;
+    m1 = fma(vel[kVelEx * Qp + i], f, m1);
+    m2 = fma(vel[kVelEy * Qp + i], f, m2);
+  }
+  d0 = double(m0);
+  d1 = double(m1);
+  d2 = double(m2);
+  for (int off = 16; off > 0; off >>= 1) {
+    d0 += __shfl_xor_sync(0xffffffffu, d0, off);
+    d1 += __shfl_xor_sync(0xffffffffu, d1, off);
+    d2 += __shfl_xor_sync(0xffffffffu, d2, off);
+  }
+}
+
+// node moments rho, u_x, u_y (FP64 outputs), one warp per node
+template <class ST>
+__global__ void moments_kernel(const void* in, const float* scale, const typename ST::R* vel, int64_t K, int Np,
                                int Qp, double* rho, double* ux, double* uy) {
   using S = typename ST::S;
+  using R = typename ST::R;
+  const int lane = threadIdx.x & 31;
   const int64_t nodes = K * Np;
-  for (int64_t kn = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; kn < nodes;
-       kn += int64_t(gridDim.x) * blockDim.x) {
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t kn = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; kn < nodes; kn += nw) {
     const S* row = static_cast<const S*>(in) + kn * Qp;
-    const double s = ST::dev ? double(scale[kn / Np]) : 0.0;
-    double m0 = 0, m1 = 0, m2 = 0;
-    for (int i = 0; i < Qp; ++i) {
-      const double f = decode64<ST>(row[i], vel64[2 * Qp + i], s);
-      m0 += f;
-      m1 += vel64[i] * f;
-      m2 += vel64[Qp + i] * f;
+    const R s = ST::dev ? R(scale[kn / Np]) : R(0);
+    double m0, m1, m2;
+    node_sums<ST>(row, vel, Qp, s, lane, m0, m1, m2);
+    if (lane == 0) {
+      rho[kn] = m0;
+      ux[kn] = m1 / m0;
+      uy[kn] = m2 / m0;
     }
-    rho[kn] = m0;
-    ux[kn] = m1 / m0;
-    uy[kn] = m2 / m0;
   }
 }
 
 // mass partial sums: sum over nodes of J_k mw_n rho; flags non-finite / rho <= 0
 template <class ST>
-__global__ void mass_partial_kernel(const void* in, const float* scale, const double* vel64, const double* Jk,
+__global__ void mass_partial_kernel(const void* in, const float* scale, const typename ST::R* vel, const double* Jk,
                                     const double* mw, int64_t K, int Np, int Qp, double* partial, int* flag) {
   using S = typename ST::S;
+  using R = typename ST::R;
   __shared__ double red[32];
+  const int lane = threadIdx.x & 31;
   const int64_t nodes = K * Np;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   double acc = 0.0;
-  for (int64_t kn = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; kn < nodes;
-       kn += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t kn = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; kn < nodes; kn += nw) {
     const S* row = static_cast<const S*>(in) + kn * Qp;
     const int64_t k = kn / Np;
-    const double s = ST::dev ? double(scale[k]) : 0.0;
-    double rho = 0.0;
-    for (int i = 0; i < Qp; ++i) rho += decode64<ST>(row[i], vel64[2 * Qp + i], s);
-    if (!(rho > 0.0) || !isfinite(rho)) atomicOr(flag, 1);
-    acc += Jk[k] * mw[kn % Np] * rho;
+    const R s = ST::dev ? R(scale[k]) : R(0);
+    double rho, m1, m2;
+    node_sums<ST>(row, vel, Qp, s, lane, rho, m1, m2);
+    if (lane == 0) {
+      if (!(rho > 0.0) || !isfinite(rho)) atomicOr(flag, 1);
+      acc += Jk[k] * mw[kn % Np] * rho;
+    }
   }
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -962,7 +997,9 @@ void launch_moments(const Group& g, int cur, const Case& cs, double* r, double* 
   const int64_t nodes = cs.K * g.Np;
   const S* in = static_cast<const S*>(g.f[cur]) + size_t(cs.k_off) * g.Np * g.Qp;
   const float* sc = g.scale[cur] ? g.scale[cur] + cs.k_off : nullptr;
-  moments_kernel<ST><<<grid_for(nodes, 256), 256, 0, st>>>(in, sc, g.vel64, cs.K, g.Np, g.Qp, r, x, y);
+  using R = typename ST::R;
+  moments_kernel<ST><<<grid_for(nodes * 32, 256), 256, 0, st>>>(in, sc, static_cast<const R*>(g.vel), cs.K, g.Np,
+                                                                  g.Qp, r, x, y);
 }
 
 int get_moments(Batch& b, int c, double* rho, double* ux, double* uy, int on_device) {
@@ -1006,8 +1043,9 @@ void launch_mass(const Group& g, int cur, const Case& cs, int blocks, cudaStream
   using S = typename ST::S;
   const S* in = static_cast<const S*>(g.f[cur]) + size_t(cs.k_off) * g.Np * g.Qp;
   const float* sc = g.scale[cur] ? g.scale[cur] + cs.k_off : nullptr;
-  mass_partial_kernel<ST><<<blocks, kMassThreads, 0, st>>>(in, sc, g.vel64, g.Jk + cs.k_off, g.mw, cs.K, g.Np, g.Qp,
-                                                           g.partial, g.flag);
+  using R = typename ST::R;
+  mass_partial_kernel<ST><<<blocks, kMassThreads, 0, st>>>(in, sc, static_cast<const R*>(g.vel), g.Jk + cs.k_off,
+                                                           g.mw, cs.K, g.Np, g.Qp, g.partial, g.flag);
 }
 
 int mass(Batch& b, int c, double* total) {
@@ -1016,7 +1054,7 @@ int mass(Batch& b, int c, double* total) {
   const Group& g = b.groups[cs.group];
   FEDBM_CK(cudaMemsetAsync(g.flag, 0, sizeof(int), b.stream));
   const int64_t nodes = cs.K * g.Np;
-  const int blocks = int(std::min<int64_t>(kMassBlocks, (nodes + kMassThreads - 1) / kMassThreads));
+  const int blocks = int(std::min<int64_t>(kMassBlocks, (nodes * 32 + kMassThreads - 1) / kMassThreads));
   switch (g.store) {
     case kStoreF64: launch_mass<StoreF64>(g, b.cur, cs, blocks, b.stream); break;
     case kStoreF32: launch_mass<StoreF32>(g, b.cur, cs, blocks, b.stream); break;
