@@ -195,27 +195,41 @@ __device__ __forceinline__ typename ST::R decode_r(const typename ST::S v, typen
 }
 
 // Sums over one node row: one warp per node, lanes on consecutive velocities
-// (coalesced), per-lane partial sums in R, the warp reduction in FP64.
+// (coalesced), partial sums and the warp reduction in the state's compute
+// precision R (FP64 for the FP64 state), returned as FP64.
 template <class ST>
 __device__ __forceinline__ void node_sums(const typename ST::S* row, const typename ST::R* vel, int Qp,
-                                          typename ST::R s, int lane, double& d0, double& d1, double& d2) {
+                                          typename ST::R s, int lane, typename ST::R& d0, typename ST::R& d1,
+                                          typename ST::R& d2) {
   using R = typename ST::R;
+  using S = typename ST::S;
+  constexpr int V = 16 / sizeof(S);  // values per 16-byte load (Qp is a multiple of 8)
   R m0 = 0, m1 = 0, m2 = 0;
-  for (int i = lane; i < Qp; i += 32) {
-    const R w = vel[kVelW * Qp + i];
-    const R f = decode_r<ST>(row[i], w, w * s);
-    m0 += f;
-    m1 = fma(vel[kVelEx * Qp + i], f, m1);
-    m2 = fma(vel[kVelEy * Qp + i], f, m2);
+  // 16-byte loads, several in flight per lane: one 128-byte load per warp at a
+  // time leaves HBM latency-bound
+#pragma unroll 4
+  for (int i = lane * V; i < Qp; i += 32 * V) {
+    __align__(16) S q[V];
+    *reinterpret_cast<uint4*>(q) = *reinterpret_cast<const uint4*>(row + i);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const R w = vel[kVelW * Qp + i + j];
+      const R f = decode_r<ST>(q[j], w, w * s);
+      m0 += f;
+      m1 = fma(vel[kVelEx * Qp + i + j], f, m1);
+      m2 = fma(vel[kVelEy * Qp + i + j], f, m2);
+    }
   }
-  d0 = double(m0);
-  d1 = double(m1);
-  d2 = double(m2);
+  // the warp reduction in R as well (FP64 throughput is low on this part; for
+  // the FP32 and 16-bit states the lane sums are FP32 already)
   for (int off = 16; off > 0; off >>= 1) {
-    d0 += __shfl_xor_sync(0xffffffffu, d0, off);
-    d1 += __shfl_xor_sync(0xffffffffu, d1, off);
-    d2 += __shfl_xor_sync(0xffffffffu, d2, off);
+    m0 += __shfl_xor_sync(0xffffffffu, m0, off);
+    m1 += __shfl_xor_sync(0xffffffffu, m1, off);
+    m2 += __shfl_xor_sync(0xffffffffu, m2, off);
   }
+  d0 = m0;
+  d1 = m1;
+  d2 = m2;
 }
 
 // node moments rho, u_x, u_y (FP64 outputs), one warp per node
@@ -230,12 +244,14 @@ __global__ void moments_kernel(const void* in, const float* scale, const typenam
   for (int64_t kn = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; kn < nodes; kn += nw) {
     const S* row = static_cast<const S*>(in) + kn * Qp;
     const R s = ST::dev ? R(scale[kn / Np]) : R(0);
-    double m0, m1, m2;
+    R m0, m1, m2;
     node_sums<ST>(row, vel, Qp, s, lane, m0, m1, m2);
     if (lane == 0) {
-      rho[kn] = m0;
-      ux[kn] = m1 / m0;
-      uy[kn] = m2 / m0;
+      // the quotients in R too: FP64 division is slow here, and the FP32 and
+      // 16-bit states carry FP32 precision
+      rho[kn] = double(m0);
+      ux[kn] = double(m1 / m0);
+      uy[kn] = double(m2 / m0);
     }
   }
 }
@@ -255,8 +271,9 @@ __global__ void mass_partial_kernel(const void* in, const float* scale, const ty
     const S* row = static_cast<const S*>(in) + kn * Qp;
     const int64_t k = kn / Np;
     const R s = ST::dev ? R(scale[k]) : R(0);
-    double rho, m1, m2;
-    node_sums<ST>(row, vel, Qp, s, lane, rho, m1, m2);
+    R rho_r, m1, m2;
+    node_sums<ST>(row, vel, Qp, s, lane, rho_r, m1, m2);
+    const double rho = double(rho_r);
     if (lane == 0) {
       if (!(rho > 0.0) || !isfinite(rho)) atomicOr(flag, 1);
       acc += Jk[k] * mw[kn % Np] * rho;
