@@ -271,7 +271,7 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
       };
       if constexpr (NTH > 0) {
         constexpr int GC = moment_lanes(NTH > 0 ? NTH : 1, 1, (QT > 0 ? QT : V) / V);
-#pragma unroll
+#pragma unroll 8
         for (int c = 0; c < (QT > 0 ? QT : V) / V; c += GC) chunk(c + lane);
       } else {
         for (int c = lane; c < nchunk; c += G) chunk(c);

@@ -291,26 +291,29 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
 
   // residual and neighbour-trace columns of (element k, velocity i), loaded
   // one pass ahead of their use
-  auto fetch = [&](int64_t k, int i, float (&rx)[NP], float (&tx)[NF]) {
+  // (the traces stay as stored, with each face's neighbour scale, and are
+  // decoded where they are used, so that nothing waits on the loads here)
+  constexpr int NSX = ST::dev ? 3 : 1;  // neighbour scales, deviation forms only
+  auto fetch = [&](int64_t k, int i, float (&rx)[NP], S (&tx)[NF], float (&sx)[NSX]) {
 #pragma unroll
     for (int n = 0; n < NP; ++n) rx[n] = read_res ? __ldg(a.res + (k * NP + n) * QT + i) : 0.f;
-    const float wi = ST::dev ? __ldg(a.vel + kVelW * QT + i) : 0.f;
 #pragma unroll
     for (int fcx = 0; fcx < 3; ++fcx) {
       const int code = __ldg(a.nbr + k * 3 + fcx);
       const int64_t kn = code >= 0 ? int64_t(code >> 3) : k;  // walls: an in-bounds address, not used
       const int fn = (code >> 1) & 3;
-      const float wsn = ST::dev ? wi * __ldg(a.scale_in + kn) : 0.f;
+      if constexpr (ST::dev) sx[fcx] = __ldg(a.scale_in + kn);
 #pragma unroll
       for (int aa = 0; aa < NFP; ++aa) {
         const int a2 = (code & 1) ? NFP - 1 - aa : aa;
         const int node = fn == 0 ? face_node(0, a2) : (fn == 1 ? face_node(1, a2) : face_node(2, a2));
-        tx[fcx * NFP + aa] = code >= 0 ? decode<ST>(fin[(kn * NP + node) * QT + i], wi, wsn) : 0.f;
+        tx[fcx * NFP + aa] = fin[(kn * NP + node) * QT + i];  // walls: not used
       }
     }
   };
-  float rcur[NP], tcur[NF];
-  if (tile < ntiles) fetch(tile, tid, rcur, tcur);
+  float rcur[NP], scur[NSX];
+  S tcur[NF];
+  if (tile < ntiles) fetch(tile, tid, rcur, tcur, scur);
 
   bool failed = false;
   int pending = -1;   // parity of a tile copy issued but not yet waited for
@@ -361,7 +364,8 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
           if (code >= 0) {
 #pragma unroll
             for (int aa = 0; aa < NFP; ++aa)
-              flux[fcx * NFP + aa] = c * (fc[face_node(fcx, aa)] - tcur[fcx * NFP + aa]);
+              flux[fcx * NFP + aa] =
+                  c * (fc[face_node(fcx, aa)] - decode<ST>(tcur[fcx * NFP + aa], w, ST::dev ? w * scur[fcx % NSX] : 0.f));
           } else {
             const int slot = -code - 1;  // wall slot: 4 * case + side
             const float fb = __ldg(a.wall_feq + slot * QT + i);
@@ -415,9 +419,10 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
         mma_commit(bar_mma);
       }
       // the next pass's (or next element's first pass's) loads fly during the MMAs
-      float rnext[NP], tnext[NF];
-      if (!last) fetch(k0, i + kTcThreads, rnext, tnext);
-      else if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x, tid, rnext, tnext);
+      float rnext[NP], snext[NSX];
+      S tnext[NF];
+      if (!last) fetch(k0, i + kTcThreads, rnext, tnext, snext);
+      else if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x, tid, rnext, tnext, snext);
 
       const bool mok = mbar_wait_bounded(bar_mma, mph, 2000000000ull);
       mph ^= 1u;
@@ -459,6 +464,10 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       for (int n = 0; n < NP; ++n) rcur[n] = rnext[n];
 #pragma unroll
       for (int q = 0; q < NF; ++q) tcur[q] = tnext[q];
+      if constexpr (ST::dev) {
+#pragma unroll
+        for (int q = 0; q < NSX; ++q) scur[q] = snext[q];
+      }
       fence_before_sync();
       __syncthreads();  // accumulators and operand rows are free for the next pass
     }
