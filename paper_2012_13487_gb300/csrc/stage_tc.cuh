@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
 #pragma unroll 1
     for (int pass = 0; pass < NPASS; ++pass) {
       const int i = pass * kTcThreads + tid;
-      const float ex = sm.vel[kVelEx * QT + i], ey = sm.vel[kVelEy * QT + i], w = __ldg(a.vel + kVelW * QT + i);
+      const float ex = sm.vel[kVelEx * QT + i], ey = sm.vel[kVelEy * QT + i];
+      const float w = ST::dev ? sm.vel[kVelW * QT + i] : __ldg(a.vel + kVelW * QT + i);  // the FP32 copy has no w row
       const float invw = ST::dev ? __ldg(a.vel + kVelInvW * QT + i) : 0.f;
       const float ar = ex * sm.geo[0] + ey * sm.geo[2], as = ex * sm.geo[1] + ey * sm.geo[3];
       float fc[NP];
