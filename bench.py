@@ -361,7 +361,7 @@ def run_ours(args, w, name):
     s = make_solver(w, st.cuda_stream, args.epc, args.tpb, args.stages, args.tc)
     s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
     if not args.no_tune and not (args.epc or args.tpb or args.stages or args.tc == 1):
-        s.autotune(None, 5)
+        s.autotune(None, 20)
     s.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -433,7 +433,7 @@ def run_ours(args, w, name):
         sb = make_solver(wb, st.cuda_stream)
         sb.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
         if not args.no_tune:
-            sb.autotune(None, 5)
+            sb.autotune(None, 20)
         ms_b = time_steps(sb.step, st, max(1, args.steps // 2), args.warmup)
         sb.close()
         bat = measure_batch(WORKLOADS["batch256_couette_cavity_fp32"], st, 10, 3, 2, not args.no_tune)
