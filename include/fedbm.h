@@ -111,12 +111,14 @@ typedef struct fedbm_params {
                               the next tile while computing one (0 = auto = 1) */
   int32_t tensor_cores;  /* stage-kernel form: 0 = tensor cores (tcgen05 TF32
                             MMAs for the Dr, Ds, LIFT contractions) for FP32
-                            and BF16 state with up to 256 padded velocities
-                            where no tile is given above, else the FMA kernel; 1 = tensor cores required (EINVAL where
-                            the form has none); -1 = FMA kernel only.  The
-                            tensor-core form exists for FP32, BF16 and FP16
-                            state with 128, 256 or 1024 padded velocities
-                            and degree <= 4                                  */
+                            and BF16 state with 128 or 256 padded velocities
+                            when no tile is given above, else the FMA kernel;
+                            1 = tensor cores required (EINVAL where the form
+                            has none); -1 = FMA kernel only.  The tensor-core
+                            form exists at degree <= 4 for FP32, BF16 and FP16
+                            state with 128, 256 or 1024 padded velocities,
+                            and for FP32 and BF16 state with 16 (eight
+                            elements stacked per MMA tile)                   */
   int32_t test_wait_timeout; /* test hook, keep 0: when 1, every stage kernel
                               waits for 16 bytes that never arrive, so its
                               bounded wait (about 3 s) runs out, the kernel

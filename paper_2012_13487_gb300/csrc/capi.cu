@@ -457,11 +457,11 @@ int configure_tc(Batch& b, Group& g) {
   if (per_sm < 1 || std::max(per_sm, by_smem) * e.tc_tmem_cols(g.Qp) > 512)
     return fail(FEDBM_EINVAL, "tensor-core stage kernel cannot be resident within tensor memory");
   g.tc = 1;
-  g.epc = 1;
-  g.tpb = 128;  // one 128-velocity MMA tile per pass
+  g.epc = g.Qp < 128 ? 128 / g.Qp : 1;  // stacked elements per tile below 128 velocities
+  g.tpb = 128;                          // one 128-row MMA tile per pass
   g.nstages = 1;
   g.smem = smem;
-  g.grid = int(std::min<int64_t>(g.K, int64_t(per_sm) * nsm));
+  g.grid = int(std::min<int64_t>((g.K + g.epc - 1) / g.epc, int64_t(per_sm) * nsm));
   drop_graphs(b);
   return FEDBM_OK;
 }
@@ -864,12 +864,14 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
          for (Group& g : b->groups) {
            const int epc = g.epc, tpb = g.tpb, st = g.nstages;
            if ((r = build_group(*b, g)) != FEDBM_OK) return r;
-           // default: tensor cores for FP32 and BF16 state up to 256 padded
-           // velocities (measured no slower than the FMA kernel there); the
-           // FP16 form's rescaling sweep and the eight dependent MMA rounds
-           // of 1024 velocities make the FMA kernel the faster one
+           // default: tensor cores for FP32 and BF16 state with 128 or 256
+           // padded velocities (measured no slower than the FMA kernel there);
+           // the FP16 form's rescaling sweep, the eight dependent MMA rounds of
+           // 1024 velocities and the few stacked tiles of small 16-velocity
+           // meshes make the FMA kernel the faster one elsewhere
            const bool want_tc = g.tc_mode > 0 || (g.tc_mode == 0 && epc == 0 && tpb == 0 && st == 0 &&
-                                                   g.store != kStoreF16 && g.Qp <= 256 && tc_available(g));
+                                                   g.store != kStoreF16 && g.Qp >= 128 && g.Qp <= 256 &&
+                                                   tc_available(g));
            if (want_tc) {
              if ((r = configure_tc(*b, g)) != FEDBM_OK) return r;
            } else if ((r = configure_tiles(*b, g, epc, tpb, st)) != FEDBM_OK) {

@@ -219,9 +219,9 @@ __host__ __device__ constexpr int moment_lanes(int nth, int epc, int nchunk) {
   return G;
 }
 
-// NTH > 0: a CTA of NTH threads and one element per tile (the tensor-core
+// NTH > 0: a CTA of NTH threads and EPC elements per tile (the tensor-core
 // kernel), so the lane grouping and the chunk loop are compile-time.
-template <class ST, class Acc, int QT, int NTH = 0>
+template <class ST, class Acc, int QT, int NTH = 0, int EPC = 1>
 __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename ST::S* s_f,
                              const float* s_scale, const typename ST::R* s_geo, typename ST::R* s_mom, int ne,
                              const typename ST::R* s_vel) {
@@ -231,7 +231,7 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
   static_assert(NTH == 0 || QT > 0, "a compile-time CTA needs a compile-time velocity count");
   const int Qp = QT > 0 ? QT : a.Qp, tid = threadIdx.x, nth = NTH > 0 ? NTH : blockDim.x;
   const int nchunk = Qp / V;
-  const int G = NTH > 0 ? moment_lanes(NTH, 1, (QT > 0 ? QT : 1) / V) : moment_lanes(nth, a.epc, nchunk);
+  const int G = NTH > 0 ? moment_lanes(NTH, EPC, (QT > 0 ? QT : 1) / V) : moment_lanes(nth, a.epc, nchunk);
   const int ngroups = nth / G, grp = tid / G, lane = tid % G;
   const int npair = ne * NP;
   const R* ex = s_vel + kVelEx * Qp;  // shared-memory copy of the velocity rows
@@ -270,7 +270,7 @@ __device__ void tile_moments(const StageArgs<typename ST::R>& a, const typename 
         m2.add(c2);
       };
       if constexpr (NTH > 0) {
-        constexpr int GC = moment_lanes(NTH > 0 ? NTH : 1, 1, (QT > 0 ? QT : V) / V);
+        constexpr int GC = moment_lanes(NTH > 0 ? NTH : 1, EPC, (QT > 0 ? QT : V) / V);
 #pragma unroll 8
         for (int c = 0; c < (QT > 0 ? QT : V) / V; c += GC) chunk(c + lane);
       } else {

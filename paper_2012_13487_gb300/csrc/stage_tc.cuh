@@ -27,7 +27,12 @@ constexpr int KL = (NF + 7) / 8 * 8;      // K of the lift MMA (face nodes)
 constexpr int NL = ND;                    // N of the lift MMA
 constexpr int KCD = KD / 4, KCL = KL / 4; // 16-byte chunks per operand row
 constexpr int CPM = 2 * ND + NL;          // accumulator columns of one 128-velocity pass
-constexpr int kTcThreads = 128;           // one MMA tile of velocities per pass
+constexpr int kTcThreads = 128;           // one MMA tile of (element, velocity) rows per pass
+
+// elements per tile: one for 128 or more velocities (in 128-velocity passes),
+// else 128 / QT elements stacked into one MMA tile (the operators are the same
+// for every element; the geometric factors enter per row in the epilogue)
+__host__ __device__ constexpr int elems_per_tile(int QT) { return QT >= kTcThreads ? 1 : kTcThreads / QT; }
 
 // tensor-memory columns of one CTA: a power of two >= 32
 constexpr int kTcCols = CPM <= 32 ? 32 : CPM <= 64 ? 64 : CPM <= 128 ? 128 : 256;
@@ -51,17 +56,18 @@ __host__ __device__ inline Layout layout(int QT, int s_bytes, int vel_rows) {
   size_t b = 0;
   o.bar = b;  b += 32;                                       // tile barrier, MMA barrier, TMEM address
   b = al(b, 128);
-  o.f = b;    b += size_t(NP) * QT * s_bytes;                 // element state tile
+  const int EPT = elems_per_tile(QT);
+  o.f = b;    b += size_t(EPT) * NP * QT * s_bytes;           // state tile
   b = al(b, 128);
   o.A = b;    b += 2 * size_t(kTcThreads) * KD * 4;           // (f - f_0) hi|lo of one pass
   o.F = b;    b += 2 * size_t(kTcThreads) * KL * 4;           // face fluxes hi|lo of one pass
   o.B = b;    b += 2 * size_t(2 * ND) * KD * 4;               // [Dr; Ds] hi|lo
   o.L = b;    b += 2 * size_t(NL) * KL * 4;                   // LIFT hi|lo
-  o.geo = b;  b += al(kGeoStrideDev * 4, 16);
-  o.nbr = b;  b += 16;
-  o.sc = b;   b += 16;                                        // element scale, new scale, max deviation
-  o.mom = b;  b += al(size_t(NP) * 8 * 4, 16);
-  o.wn = b;   b += al(size_t(NF) * 4, 16);
+  o.geo = b;  b += al(size_t(EPT) * kGeoStrideDev * 4, 16);
+  o.nbr = b;  b += al(size_t(EPT) * 3 * 4, 16);
+  o.sc = b;   b += al(size_t(EPT + 2) * 4, 16);              // element scales, new scale, max deviation
+  o.mom = b;  b += al(size_t(EPT) * NP * 8 * 4, 16);
+  o.wn = b;   b += al(size_t(EPT) * NF * 4, 16);
   o.vel = b;  b += al(size_t(vel_rows) * QT * 4, 16);
   o.end = b;
   return o;
@@ -168,21 +174,22 @@ __host__ __device__ constexpr bool keeps_scale() {
 
 }  // namespace tc
 
-// Bulk copies of one element's state tile and geometry (warp 0); the lanes
-// also store its three face codes (and, for the deviation forms, its scale and
-// a zero running maximum).  Every lane arrives on the barrier, so the plain
-// stores are visible to the threads that wait on it.
+// Bulk copies of one tile's state and geometry (warp 0): elements k0 ..
+// k0 + ne - 1; the lanes also store their face codes (and, for the deviation
+// forms, their scales and a zero running maximum).  Every lane arrives on the
+// barrier, so the plain stores are visible to the threads that wait on it.
 template <class ST>
 __device__ __forceinline__ void tc_issue_tile(const StageArgs<float>& a, StageSmem<float, typename ST::S>& sm,
-                                              int QT, int64_t k0) {
+                                              int QT, int64_t k0, int ne) {
   using S = typename ST::S;
   const int lane = threadIdx.x & 31;
-  if (lane < 3) sm.nbr[lane] = __ldg(a.nbr + k0 * 3 + lane);
+  for (int v = lane; v < 3 * ne; v += 32) sm.nbr[v] = __ldg(a.nbr + k0 * 3 + v);
   if constexpr (ST::dev) {
-    if (lane == 3) sm.scale[0] = __ldg(a.scale_in + k0);
-    if (lane == 4) sm.dmax[0] = 0u;
+    for (int v = lane; v < ne; v += 32) sm.scale[v] = __ldg(a.scale_in + k0 + v);
+    if (lane == 0) sm.dmax[0] = 0u;
   }
-  const uint32_t tile_bytes = uint32_t(NP * QT * sizeof(S)), geo_bytes = uint32_t(kGeoStrideDev * 4);
+  const uint32_t tile_bytes = uint32_t(size_t(ne) * NP * QT * sizeof(S));
+  const uint32_t geo_bytes = uint32_t(ne * kGeoStrideDev * 4);
   mbar_arrive_expect_tx(sm.bar, lane == 0 ? tile_bytes + geo_bytes + a.extra_tx : 0u);
   if (lane == 0) {
     bulk_load(sm.f, static_cast<const S*>(a.f_in) + k0 * NP * QT, tile_bytes, sm.bar);
@@ -210,8 +217,10 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   // found after every velocity is done, and a second encoding sweep.
   constexpr bool kKeepScale = tc::keeps_scale<ST>();
   constexpr bool kRescale = ST::dev && !kKeepScale;
-  static_assert(QT % kTcThreads == 0, "whole 128-velocity passes");
-  constexpr int NPASS = QT / kTcThreads;
+  static_assert(QT % kTcThreads == 0 || kTcThreads % QT == 0, "whole passes or whole stacked elements");
+  constexpr int EPT = elems_per_tile(QT);                       // elements per tile
+  constexpr int NPASS = QT >= kTcThreads ? QT / kTcThreads : 1;  // 128-row passes per tile
+  static_assert(EPT == 1 || !kRescale, "the rescaling form works one element at a time");
   extern __shared__ __align__(128) unsigned char smem[];  // operands need 16-byte alignment
   const Layout o = layout(QT, int(sizeof(S)), VROWS);
   uint64_t* bar_tile = reinterpret_cast<uint64_t*>(smem + o.bar);
@@ -229,8 +238,8 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   sm.geo = reinterpret_cast<float*>(smem + o.geo);
   sm.nbr = reinterpret_cast<int*>(smem + o.nbr);
   sm.scale = reinterpret_cast<float*>(smem + o.sc);       // element scale (deviation forms)
-  sm.nscale = sm.scale + 1;                                // its new scale
-  sm.dmax = reinterpret_cast<unsigned*>(sm.scale + 2);     // max |f_new/w - 1| as float bits
+  sm.nscale = sm.scale + EPT;                              // the new scale (one element)
+  sm.dmax = reinterpret_cast<unsigned*>(sm.scale + EPT + 1);  // max |f_new/w - 1| as float bits
   sm.mom = reinterpret_cast<float*>(smem + o.mom);
   sm.wn = reinterpret_cast<float*>(smem + o.wn);
   sm.vel = reinterpret_cast<float*>(smem + o.vel);
@@ -239,7 +248,11 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   const float rkA = a.rkA, rkB = a.rkB, ab = a.ab;
   const bool read_res = rkA != 0.f;
   const bool third = a.eq_order == 3;
-  const int64_t ntiles = a.K;  // one element per tile
+  const int64_t ntiles = (a.K + EPT - 1) / EPT;
+  // this thread's row of a tile: element te of the tile, velocity lane ti
+  const int te = QT >= kTcThreads ? 0 : int(threadIdx.x) / QT;
+  const int ti = QT >= kTcThreads ? int(threadIdx.x) : int(threadIdx.x) % QT;
+  auto tile_ne = [&](int64_t t) { return int(min(int64_t(EPT), a.K - t * EPT)); };
   const S* fin = static_cast<const S*>(a.f_in);
   S* fout = static_cast<S*>(a.f_out);
 
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   const uint32_t tmem = *tslot;
 
   int64_t tile = blockIdx.x;
-  if (tid < 32 && tile < ntiles) tc_issue_tile<ST>(a, sm, QT, tile);
+  if (tid < 32 && tile < ntiles) tc_issue_tile<ST>(a, sm, QT, tile * EPT, tile_ne(tile));
 
   // matrix descriptors of the operand starts; a byte offset d inside an operand
   // adds d >> 4 to the start-address field (all operands lie below 256 KB)
@@ -311,15 +324,19 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       }
     }
   };
+  // element of this thread's row in tile t (the last element for a ragged tail)
+  auto row_elem = [&](int64_t t) { return min(t * EPT + te, a.K - 1); };
   float rcur[NP], scur[NSX];
   S tcur[NF];
-  if (tile < ntiles) fetch(tile, tid, rcur, tcur, scur);
+  if (tile < ntiles) fetch(row_elem(tile), ti, rcur, tcur, scur);
 
   bool failed = false;
   int pending = -1;   // parity of a tile copy issued but not yet waited for
   uint32_t mph = 0;   // phase of the MMA barrier
   for (int j = 0; tile < ntiles; ++j, tile += gridDim.x) {
-    const int64_t k0 = tile;
+    const int ne = tile_ne(tile);
+    const bool valid = te < ne;                  // a ragged tail leaves rows empty
+    const int64_t k0 = tile * EPT + te;          // this row's element
     const bool ok = mbar_wait_bounded(bar_tile, uint32_t(j & 1), 2000000000ull);
     if (__syncthreads_or(!ok)) {
       failed = true;
@@ -329,39 +346,41 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
 
     // ---- node moments and wall numerators (as in the FMA kernel) -----------------
     if (!a.collision) {
-      for (int v = tid; v < NP * 8; v += kTcThreads) sm.mom[v] = 0.f;
+      for (int v = tid; v < EPT * NP * 8; v += kTcThreads) sm.mom[v] = 0.f;
     } else if (a.red == kRedFP64) {
-      tile_moments<ST, AccD, QT, kTcThreads>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
+      tile_moments<ST, AccD, QT, kTcThreads, EPT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
     } else if (a.red == kRedCompFP32) {
-      tile_moments<ST, AccN, QT, kTcThreads>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
+      tile_moments<ST, AccN, QT, kTcThreads, EPT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
     } else {
-      tile_moments<ST, AccF, QT, kTcThreads>(a, sm.f, sm.scale, sm.geo, sm.mom, 1, sm.vel);
+      tile_moments<ST, AccF, QT, kTcThreads, EPT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
     }
-    if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, 1, sm.vel);
+    if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, ne, sm.vel);
     __syncthreads();
-    const float dt = sm.geo[kGeoDt], inv_tau = sm.geo[kGeoInvTau];
-    const float s_el = ST::dev ? sm.scale[0] : 0.f;
+    const float* geo = sm.geo + te * kGeoStrideDev;  // this row's element
+    const float dt = geo[kGeoDt], inv_tau = geo[kGeoInvTau];
+    const float s_el = ST::dev ? sm.scale[te] : 0.f;
     const float inv_s_el = ST::dev ? 1.0f / s_el : 0.f;
-    if (kKeepScale && tid == 0) a.scale_out[k0] = s_el;
+    if (kKeepScale && valid && ti == 0) a.scale_out[k0] = s_el;
     float dloc = 0.f;  // FP16 form: this thread's max |f_new/w - 1|
 
 #pragma unroll 1
     for (int pass = 0; pass < NPASS; ++pass) {
-      const int i = pass * kTcThreads + tid;
+      const int i = pass * kTcThreads + ti;
       const float ex = sm.vel[kVelEx * QT + i], ey = sm.vel[kVelEy * QT + i];
       const float w = ST::dev ? sm.vel[kVelW * QT + i] : __ldg(a.vel + kVelW * QT + i);  // the FP32 copy has no w row
       const float invw = ST::dev ? __ldg(a.vel + kVelInvW * QT + i) : 0.f;
-      const float ar = ex * sm.geo[0] + ey * sm.geo[2], as = ex * sm.geo[1] + ey * sm.geo[3];
+      const float ar = ex * geo[0] + ey * geo[2], as = ex * geo[1] + ey * geo[3];
+      const S* frow = sm.f + te * NP * QT + i;
       float fc[NP];
 #pragma unroll
-      for (int m = 0; m < NP; ++m) fc[m] = decode<ST>(sm.f[m * QT + i], w, w * s_el);
+      for (int m = 0; m < NP; ++m) fc[m] = valid ? decode<ST>(frow[m * QT], w, w * s_el) : 0.f;
       {
         float flux[NF];
 #pragma unroll
         for (int fcx = 0; fcx < 3; ++fcx) {
-          const float en = ex * sm.geo[4 + 3 * fcx] + ey * sm.geo[5 + 3 * fcx];
-          const float c = 0.5f * (en - ab * fabsf(en)) * sm.geo[6 + 3 * fcx];
-          const int code = sm.nbr[fcx];
+          const float en = ex * geo[4 + 3 * fcx] + ey * geo[5 + 3 * fcx];
+          const float c = valid ? 0.5f * (en - ab * fabsf(en)) * geo[6 + 3 * fcx] : 0.f;  // empty rows: no flux
+          const int code = valid ? sm.nbr[te * 3 + fcx] : 0;
           if (code >= 0) {
 #pragma unroll
             for (int aa = 0; aa < NFP; ++aa)
@@ -376,7 +395,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
             // incoming velocities take the wall state; outgoing ones have no jump
 #pragma unroll
             for (int aa = 0; aa < NFP; ++aa) {
-              const float fp = diffuse ? sm.wn[fcx * NFP + aa] * scale : fb;
+              const float fp = diffuse ? sm.wn[te * NF + fcx * NFP + aa] * scale : fb;
               flux[fcx * NFP + aa] = en < 0.f ? c * (fc[face_node(fcx, aa)] - fp) : 0.f;
             }
           }
@@ -390,7 +409,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
 
       const bool last = pass == NPASS - 1;
       if (!kRescale && last && tile + gridDim.x < ntiles) {
-        if (tid < 32) tc_issue_tile<ST>(a, sm, QT, tile + gridDim.x);
+        if (tid < 32) tc_issue_tile<ST>(a, sm, QT, (tile + gridDim.x) * EPT, tile_ne(tile + gridDim.x));
         pending = (j + 1) & 1;
       }
       // two threads in different warps issue the two products side by side
@@ -423,7 +442,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       float rnext[NP], snext[NSX];
       S tnext[NF];
       if (!last) fetch(k0, i + kTcThreads, rnext, tnext, snext);
-      else if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x, tid, rnext, tnext, snext);
+      else if (tile + gridDim.x < ntiles) fetch(row_elem(tile + gridDim.x), ti, rnext, tnext, snext);
 
       const bool mok = mbar_wait_bounded(bar_mma, mph, 2000000000ull);
       mph ^= 1u;
@@ -444,9 +463,9 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int n = 8 * c + q;
-          if (n < NP) {
+          if (n < NP && valid) {
             float rhs = fmaf(-ar, V[q], fmaf(-as, W[q], Lf[q]));
-            rhs += collision<float>(sm.mom + n * 8, ex, ey, w, fc[n], inv_tau, third);
+            rhs += collision<float>(sm.mom + (te * NP + n) * 8, ex, ey, w, fc[n], inv_tau, third);
             float r = dt * rhs;
             if (read_res) r = fmaf(rkA, rcur[n], r);
             a.res[(k0 * NP + n) * QT + i] = r;
@@ -505,7 +524,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       }
       __syncthreads();  // the state tile, scale and maximum are free for the next element
       if (tile + gridDim.x < ntiles) {
-        if (tid < 32) tc_issue_tile<ST>(a, sm, QT, tile + gridDim.x);
+        if (tid < 32) tc_issue_tile<ST>(a, sm, QT, (tile + gridDim.x) * EPT, tile_ne(tile + gridDim.x));
         pending = (j + 1) & 1;
       }
     }
@@ -528,7 +547,8 @@ constexpr int kTcMaxP = 4;
 
 // Dynamic shared memory of the tensor-core kernel (0 = no tensor-core form).
 size_t tc_smem(int store_kind, int Qp) {
-  if (P > kTcMaxP || store_kind == kStoreF64 || (Qp != 128 && Qp != 256 && Qp != 1024)) return 0;
+  if (P > kTcMaxP || store_kind == kStoreF64 || (Qp != 16 && Qp != 128 && Qp != 256 && Qp != 1024)) return 0;
+  if (Qp == 16 && store_kind == kStoreF16) return 0;  // stacked tiles: not the rescaling form
   const bool dev = store_kind != kStoreF32;
   return tc::layout(Qp, dev ? 2 : 4, dev ? 3 : 2).end;
 }
@@ -542,6 +562,8 @@ cudaError_t with_tc_kernel(int store_kind, int Qp, Fn fn) {
   if constexpr (P <= kTcMaxP) {
     auto by_q = [&](auto st) -> cudaError_t {
       using ST = decltype(st);
+      if constexpr (!ST::dev || tc::keeps_scale<ST>())
+        if (Qp == 16) return fn(stage_kernel_tc<ST, 16>);
       if (Qp == 256) return fn(stage_kernel_tc<ST, 256>);
       if (Qp == 128) return fn(stage_kernel_tc<ST, 128>);
       if (Qp == 1024) return fn(stage_kernel_tc<ST, 1024>);

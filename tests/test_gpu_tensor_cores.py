@@ -1,7 +1,8 @@
 """Tensor-core form of the stage kernel (tcgen05 TF32 MMAs with a hi/lo split
 for the Dr, Ds and LIFT contractions) against the FP64 oracle and against the
 FMA form, on the shapes it serves: FP32 state or BF16/FP16 deviation state,
-128, 256 or 1024 padded velocities, degree <= 4."""
+128, 256 or 1024 padded velocities, degree <= 4, and 16 velocities (FP32, BF16)
+with eight elements stacked into one 128-row MMA tile."""
 import numpy as np
 import pytest
 
@@ -60,14 +61,14 @@ def test_tc_default_selection_and_rejection():
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32").info.tensor_cores == 1
     # explicit FMA tiles, other velocity counts, FP64 state, degree 5: FMA form
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32", epc=2).info.tensor_cores == 0
-    assert cases.solver(cases.cavity(3, 3, 4, velset=("gh", 4)), "fp32").info.tensor_cores == 0
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("gh", 5)), "fp32").info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "bf16").info.tensor_cores == 1
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp64").info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp16").info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp16", tc=1).info.tensor_cores == 1
     assert cases.solver(cases.cavity(3, 3, 5, velset=("nc", 16)), "fp32").info.tensor_cores == 0
-    with pytest.raises(fb.FedbmError) as e:
-        cases.solver(cases.cavity(3, 3, 4, velset=("gh", 4)), "fp32", tc=1)
+    with pytest.raises(fb.FedbmError) as e:   # 25 velocities padded to 32: no tensor-core form
+        cases.solver(cases.cavity(3, 3, 4, velset=("gh", 5)), "fp32", tc=1)
     assert e.value.code == fb.FEDBM_EINVAL
 
 
@@ -111,7 +112,7 @@ def test_tc_wait_timeout_reported():
 def test_tc_batch_groups_toggle_bitwise_with_single_solvers():
     from paper_2012_13487_gb300 import fedbm as fb
     cs = [cases.cavity(4, 3, 4, velset=("nc", 16), kn=1.0), cases.couette(5, 2, 2, velset=("nc", 16), kn=2.0),
-          cases.cavity(3, 3, 3, velset=("gh", 4))]
+          cases.cavity(3, 3, 3, velset=("gh", 5))]
     b = cases.batch(cs, "fp32")
     prs = [cases.oracle_problem(c) for c in cs]
     f0s = [cases.initial_state(pr, amp=1e-2, seed=21 + j) for j, pr in enumerate(prs)]
@@ -158,3 +159,28 @@ def test_tc_deviation_forms(prec, u, p, vs):
     for tc in (1, -1):
         assert (np.abs(out[tc] - f1) / (w * md)).max() < 12 * u
     assert (np.abs(out[1] - out[-1]) / (w * md)).max() < 12 * u
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("nx,ny", [(4, 4), (3, 3)])   # 32 elements, and 18 (a ragged last tile of 2)
+def test_tc_stacked_gh16_fp32(p, nx, ny):
+    c = cases.cavity(nx, ny, p, velset=("gh", 4), kn=1.0, eq_order=3)
+    pr, s, f0, f_tc = _pair(c, 6, tc=1)
+    assert s.info.tensor_cores == 1 and s.info.Q_padded == 16 and s.info.elems_per_cta == 8
+    assert cases.rel_max_err(f_tc, pr.run(f0, 6)) < fp32_tol(pr, 30)
+    _, _, _, f_fma = _pair(c, 6, tc=-1)
+    assert cases.rel_max_err(f_tc, f_fma) < fp32_tol(pr, 30)
+
+
+def test_tc_stacked_gh16_couette_bf16():
+    c = cases.couette(5, 3, 3, velset=("gh", 4), kn=0.5)
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=1e-2, seed=43)
+    s = cases.solver(c, "bf16", tc=1)
+    assert s.info.tensor_cores == 1 and s.info.elems_per_cta == 8
+    s.set_state(f0)
+    s.step(2)
+    f1 = pr.run(f0, 2)
+    w = pr.w[None, None, :]
+    md = np.abs(f1 / w - 1.0).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(s.state() - f1) / (w * md)).max() < 12 * 2.0 ** -8
