@@ -42,6 +42,9 @@ WORKLOADS = {
         kind="cavity", nx=64, ny=64, p=4, vel=("nc", 16), kn=1.0, speed=0.1, precision="bf16",
         desc="lid-driven cavity Kn=1, 64x64x2 triangles, p=4, NC 16x16 on [-4,4]sqrt(RT), lid 0.1, "
              "BF16 deviation state"),
+    "cavity_kn1_64x64x2_p5_nc16x16_fp32": dict(
+        kind="cavity", nx=64, ny=64, p=5, vel=("nc", 16), kn=1.0, speed=0.1, precision="fp32",
+        desc="lid-driven cavity Kn=1, 64x64x2 triangles, p=5, NC 16x16 on [-4,4]sqrt(RT), lid 0.1, FP32"),
     "cavity_kn1_64x64x2_p4_gh16_fp32": dict(
         kind="cavity", nx=64, ny=64, p=4, vel=("gh", 4), kn=1.0, speed=0.1, precision="fp32",
         desc="lid-driven cavity Kn=1, 64x64x2 triangles, p=4, GH D2Q16, lid 0.1, FP32"),

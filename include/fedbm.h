@@ -112,10 +112,11 @@ typedef struct fedbm_params {
   int32_t tensor_cores;  /* stage-kernel form: 0 = tensor cores (tcgen05 TF32
                             MMAs for the Dr, Ds, LIFT contractions) for FP32
                             and BF16 state with 128 or 256 padded velocities
-                            when no tile is given above, else the FMA kernel;
+                            at degree <= 4 when no tile is given above, else
+                            the FMA kernel;
                             1 = tensor cores required (EINVAL where the form
                             has none); -1 = FMA kernel only.  The tensor-core
-                            form exists at degree <= 4 for FP32, BF16 and FP16
+                            form exists at degree <= 5 for FP32, BF16 and FP16
                             state with 128, 256 or 1024 padded velocities,
                             and for FP32 and BF16 state with 16 (eight
                             elements stacked per MMA tile)                   */

@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
 }
 
 // Largest degree with a tensor-core form.
-constexpr int kTcMaxP = 4;
+constexpr int kTcMaxP = 5;
 
 // Dynamic shared memory of the tensor-core kernel (0 = no tensor-core form).
 size_t tc_smem(int store_kind, int Qp) {

@@ -1,7 +1,7 @@
 """Tensor-core form of the stage kernel (tcgen05 TF32 MMAs with a hi/lo split
 for the Dr, Ds and LIFT contractions) against the FP64 oracle and against the
 FMA form, on the shapes it serves: FP32 state or BF16/FP16 deviation state,
-128, 256 or 1024 padded velocities, degree <= 4, and 16 velocities (FP32, BF16)
+128, 256 or 1024 padded velocities, degree <= 5, and 16 velocities (FP32, BF16)
 with eight elements stacked into one 128-row MMA tile."""
 import numpy as np
 import pytest
@@ -26,7 +26,7 @@ def _pair(c, nsteps, amp=1e-2, seed=17, reduction="default", **tile):
     return pr, s, f0, s.state()
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_tc_cavity_nc16_matches_oracle_and_fma(p):
     c = cases.cavity(5, 4, p, velset=("nc", 16), kn=1.0)
     pr, s, f0, f_tc = _pair(c, 6, tc=1)
@@ -59,7 +59,7 @@ def test_tc_1024_velocities_cavity_kn8(p):
 def test_tc_default_selection_and_rejection():
     from paper_2012_13487_gb300 import fedbm as fb
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32").info.tensor_cores == 1
-    # explicit FMA tiles, other velocity counts, FP64 state, degree 5: FMA form
+    # explicit FMA tiles, other velocity counts, FP64 state, degree >= 5: FMA form
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32", epc=2).info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("gh", 5)), "fp32").info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "bf16").info.tensor_cores == 1
@@ -67,6 +67,8 @@ def test_tc_default_selection_and_rejection():
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp16").info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp16", tc=1).info.tensor_cores == 1
     assert cases.solver(cases.cavity(3, 3, 5, velset=("nc", 16)), "fp32").info.tensor_cores == 0
+    assert cases.solver(cases.cavity(3, 3, 5, velset=("nc", 16)), "fp32", tc=1).info.tensor_cores == 1
+    assert cases.solver(cases.cavity(3, 3, 6, velset=("nc", 16)), "fp32").info.tensor_cores == 0
     with pytest.raises(fb.FedbmError) as e:   # 25 velocities padded to 32: no tensor-core form
         cases.solver(cases.cavity(3, 3, 4, velset=("gh", 5)), "fp32", tc=1)
     assert e.value.code == fb.FEDBM_EINVAL
