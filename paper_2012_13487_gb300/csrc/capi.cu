@@ -496,10 +496,11 @@ int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
 
 // ---- tile autotuner ------------------------------------------------------------
 // For every group, time each candidate (elements per CTA, threads per CTA,
-// pipeline stages) on `trials` launches of RK stage 2 (the residual-reading
-// form) and keep the fastest.  The kernel reads f[cur] and writes f[1-cur] and
-// the residual, so the current state is untouched; the residual's contents
-// are overwritten by the next step's first stage, which does not read it.
+// pipeline stages, kernel form) on `trials` step-shaped rounds (RK stage 1,
+// which reads no residual, then four launches of stage 2, which does) and keep
+// the fastest.  Every launch reads f[cur] and writes f[1-cur] and the
+// residual, so the current state is untouched; the residual's contents are
+// overwritten by the next step's first stage, which does not read it.
 // Results are cached per (device, degree, velocity count, precision,
 // element count) in a flat JSON object, one entry per line.
 struct TuneEntry {
@@ -573,10 +574,15 @@ int autotune(Batch& b, const char* cache_path, int trials) {
     }
     TuneEntry best;
     best.us = 1e300;
+    // a trial is one step's mix: stage 0 (no residual read) and four
+    // residual-reading launches, all from f[cur]
     auto time_current = [&](TuneEntry cand) {
       if (launch_stage(g, 1, b.cur, b.stream) != cudaSuccess) return;  // warm-up
       cudaEventRecord(e0, b.stream);
-      for (int t = 0; t < trials; ++t) launch_stage(g, 1, b.cur, b.stream);
+      for (int t = 0; t < trials; ++t) {
+        launch_stage(g, 0, b.cur, b.stream);
+        for (int r = 0; r < 4; ++r) launch_stage(g, 1, b.cur, b.stream);
+      }
       cudaEventRecord(e1, b.stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) return;
       float ms = 0.f;
