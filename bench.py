@@ -311,6 +311,38 @@ def job_throughput(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
+def pick_form(w, st, torch, steps=100):
+    """Autotune the FMA form and, where the workload has one, the tensor-core
+    form, time `steps` steps of each and keep the faster solver (the two are
+    within a few per cent on some shapes, closer than the autotuner's short
+    trials resolve)."""
+    from paper_2012_13487_gb300 import fedbm as fb
+    best, best_ms = None, None
+    for tc in (-1, 1):
+        try:
+            s = make_solver(w, st.cuda_stream, tc=tc)
+        except fb.FedbmError:
+            continue            # no tensor-core form for this shape
+        s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+        s.autotune(None, 20)
+        s.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        s.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if best_ms is None or ms < best_ms:
+            if best is not None:
+                best.close()
+            best, best_ms = s, ms
+        else:
+            s.close()
+    best.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+    return best
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -361,10 +393,13 @@ def run_ours(args, w, name):
         return run_batch_workload(args, w, name, st, world, rank, dist)
     K, Np, Q = dims(w)
     dof = K * Np * Q
-    s = make_solver(w, st.cuda_stream, args.epc, args.tpb, args.stages, args.tc)
-    s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
-    if not args.no_tune and not (args.epc or args.tpb or args.stages or args.tc == 1):
-        s.autotune(None, 20)
+    if not args.no_tune and not (args.epc or args.tpb or args.stages or args.tc):
+        s = pick_form(w, st, torch)
+    else:
+        s = make_solver(w, st.cuda_stream, args.epc, args.tpb, args.stages, args.tc)
+        s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+        if not args.no_tune and not (args.epc or args.tpb or args.stages or args.tc == 1):
+            s.autotune(None, 20)
     s.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -433,10 +468,11 @@ def run_ours(args, w, name):
         # the three forms of the metric: FP32 state (this line), BF16 deviation
         # state on the same mesh, and the seeded 256-case batch
         wb = dict(w, precision="bf16", desc=w["desc"].replace("FP32", "BF16 deviation state"))
-        sb = make_solver(wb, st.cuda_stream)
-        sb.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
         if not args.no_tune:
-            sb.autotune(None, 20)
+            sb = pick_form(wb, st, torch)
+        else:
+            sb = make_solver(wb, st.cuda_stream)
+            sb.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
         ms_b = time_steps(sb.step, st, max(1, args.steps // 2), args.warmup)
         sb.close()
         bat = measure_batch(WORKLOADS["batch256_couette_cavity_fp32"], st, 10, 3, 2, not args.no_tune)
