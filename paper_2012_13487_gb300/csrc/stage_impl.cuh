@@ -686,6 +686,8 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
       } else {
         if (a.red == kRedFP64) tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
         else if (a.red == kRedCompFP32) tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
+        else if (QT >= 128 && nth == 128 && epc == 1)  // the usual large-Q tile: compile-time lanes
+          tile_moments<ST, AccF, QT, (QT >= 128 ? 128 : 0), 1>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
         else tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
       }
     }
