@@ -681,14 +681,24 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
     if (!a.collision) {
       for (int v = tid; v < ne * NP * 8; v += nth) sm.mom[v] = R(0);
     } else {
+      // the usual large-Q tiles (one element, 128 or 256 threads) take the
+      // moment reduction with compile-time lane groups and an unrolled loop
+      auto moments = [&](auto acc) {
+        using Acc = decltype(acc);
+        constexpr int kBig = QT >= 128 ? 1 : 0;
+        if (kBig && epc == 1 && nth == 128)
+          tile_moments<ST, Acc, QT, kBig * 128, 1>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
+        else if (kBig && epc == 1 && nth == 256)
+          tile_moments<ST, Acc, QT, kBig * 256, 1>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
+        else
+          tile_moments<ST, Acc, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
+      };
       if constexpr (sizeof(R) == 8) {
-        tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
+        moments(AccD{});
       } else {
-        if (a.red == kRedFP64) tile_moments<ST, AccD, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
-        else if (a.red == kRedCompFP32) tile_moments<ST, AccN, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
-        else if (QT >= 128 && nth == 128 && epc == 1)  // the usual large-Q tile: compile-time lanes
-          tile_moments<ST, AccF, QT, (QT >= 128 ? 128 : 0), 1>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
-        else tile_moments<ST, AccF, QT>(a, sm.f, sm.scale, sm.geo, sm.mom, ne, sm.vel);
+        if (a.red == kRedFP64) moments(AccD{});
+        else if (a.red == kRedCompFP32) moments(AccN{});
+        else moments(AccF{});
       }
     }
     // ---- 3. wall numerators ------------------------------------------------------
