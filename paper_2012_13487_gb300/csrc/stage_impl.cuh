@@ -551,7 +551,7 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
 // (65536 / (256 * min)) so that the unrolled node loop does not spill.
 template <class ST, int QT>
 __host__ __device__ constexpr int stage_min_blocks() {
-  return sizeof(typename ST::R) == 8 ? 2 : items_vpt<ST, QT>() == 2 ? 2 : (P <= 3 ? 4 : (P <= 5 ? 3 : 2));
+  return sizeof(typename ST::R) == 8 ? 2 : items_vpt<ST, QT>() == 2 ? 2 : (P <= 3 || P == 5 ? 3 : 2);
 }
 
 
