@@ -1,6 +1,7 @@
 // C ABI of the solver: set-up, state transfer, LSRK stepping (CUDA graphs of
 // the fused stage kernel), moments and the FP64 mass diagnostic.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -14,6 +15,17 @@
 #include "fedbm.h"
 #include "host_setup.h"
 #include "stage_dispatch.h"
+
+namespace {
+// NVTX range over one library call (shown by Nsight timelines; a no-op when no
+// tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 namespace fedbm {
 namespace {
@@ -552,6 +564,7 @@ void write_tune_cache(const char* path, const std::vector<std::pair<std::string,
 }
 
 int autotune(Batch& b, const char* cache_path, int trials) {
+  NvtxRange nvtx("fedbm autotune");
   if (trials < 1) trials = 5;
   auto cache = read_tune_cache(cache_path);
   bool dirty = false;
@@ -930,6 +943,7 @@ int encode_case(Batch& b, int c, const double* src) {
 }
 
 int set_state(Batch& b, int c, const double* f, int on_device) {
+  NvtxRange nvtx("fedbm set_state");
   if (!f) return fail(FEDBM_EINVAL, "null state pointer");
   const Case& cs = b.cases[c];
   const Group& g = b.groups[cs.group];
@@ -969,6 +983,7 @@ void launch_decode(const Group& g, int cur, const Case& cs, double* dst, cudaStr
 }
 
 int get_state(Batch& b, int c, double* f, int on_device) {
+  NvtxRange nvtx("fedbm get_state");
   if (!f) return fail(FEDBM_EINVAL, "null output");
   const Case& cs = b.cases[c];
   const Group& g = b.groups[cs.group];
@@ -1029,6 +1044,7 @@ void launch_moments(const Group& g, int cur, const Case& cs, double* r, double* 
 }
 
 int get_moments(Batch& b, int c, double* rho, double* ux, double* uy, int on_device) {
+  NvtxRange nvtx("fedbm get_moments");
   const Case& cs = b.cases[c];
   const Group& g = b.groups[cs.group];
   const int64_t nodes = cs.K * g.Np;
@@ -1075,6 +1091,7 @@ void launch_mass(const Group& g, int cur, const Case& cs, int blocks, cudaStream
 }
 
 int mass(Batch& b, int c, double* total) {
+  NvtxRange nvtx("fedbm mass");
   if (!total) return fail(FEDBM_EINVAL, "null output");
   const Case& cs = b.cases[c];
   const Group& g = b.groups[cs.group];
@@ -1100,6 +1117,7 @@ int mass(Batch& b, int c, double* total) {
 }
 
 int rk_step(Batch& b, int nsteps) {
+  NvtxRange nvtx("fedbm rk_step");
   if (nsteps < 0) return fail(FEDBM_EINVAL, "nsteps must be >= 0");
   int rc = build_graphs(b);
   if (rc) return rc;

@@ -210,3 +210,14 @@ def test_full_size_cavity_nc16_sampled_two_stages():
     tol = fp32_tol(pr, 2) * scale
     assert np.abs(f1_gpu[sample] - f1[sample]).max() <= tol
     assert np.abs(f2_gpu[sample] - f2_s).max() <= tol
+
+
+@pytest.mark.parametrize("vs,p,sqrt2", [(("nc", 33), 3, True), (("gh", 18), 2, False)])
+def test_largest_velocity_sets_fp32(vs, p, sqrt2):
+    """The paper's largest sets (NC 33x33 = D2Q1089 on the sqrt(2RT) grid,
+    GH D2Q324) through the runtime-stride kernel: 1089 and 324 velocities pad to
+    1096 and 328 (no compile-time stride)."""
+    c = cases.cavity(2, 2, p, velset=vs, kn=2.0, nc_sqrt2=sqrt2)
+    pr, s, f0, f_gpu, f_or = _run_pair(c, 2, "fp32", amp=1e-2)
+    assert s.info.Q == vs[1] ** 2 and s.info.Q_padded % 8 == 0
+    assert cases.rel_max_err(f_gpu, f_or) < fp32_tol(pr, 10)
