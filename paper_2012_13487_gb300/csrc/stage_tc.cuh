@@ -1,13 +1,15 @@
-// Tensor-core form of the stage kernel (FP32 state or BF16/FP16 deviation state
-// with FP32 arithmetic; QT = 128, 256 or 1024 velocities; 128 threads, one
-// velocity per thread in each 128-velocity pass).  Included by stage_impl.cuh inside its namespace:
-// it reuses the tile loads, node moments, wall numerators and collision term of
-// the FMA kernel and replaces the element-local contractions of phase 4,
+// Tensor-core form of the stage kernel: FP32 state or BF16/FP16 deviation
+// state, FP32 arithmetic; 128 threads per CTA.  QT = 128, 256 or 1024
+// velocities run in 128-velocity passes (one velocity per thread); QT = 16
+// stacks eight elements into one 128-row tile.  Included by stage_impl.cuh
+// inside its namespace: it reuses the tile loads, node moments, wall numerators
+// and collision term of the FMA kernel and replaces the element-local
+// contractions of phase 4,
 //   V = (f - f_0 1) Dr^T,  W = (f - f_0 1) Ds^T,  Lf = flux LIFT^T,
-// by tcgen05 MMAs (kind::tf32, M = 128 velocities per MMA, accumulators in
-// tensor memory).  Subtracting the first node's value f_0 changes nothing in
-// exact arithmetic (Dr 1 = Ds 1 = 0, the derivative of a constant) and keeps
-// the operands small.  Each FP32 operand x is split into x_hi = tf32(x) and
+// by tcgen05 MMAs (kind::tf32, M = 128 rows per MMA, accumulators in tensor
+// memory).  Subtracting the first node's value f_0 changes nothing in exact
+// arithmetic (Dr 1 = Ds 1 = 0, the derivative of a constant) and keeps the
+// operands small.  Each FP32 operand x is split into x_hi = tf32(x) and
 // x_lo = x - x_hi (read by the MMA as TF32) and every product is taken as
 // a_hi b_hi + a_lo b_hi + a_hi b_lo (three MMAs), which keeps the contraction
 // error near FP32 rounding of the operands.
@@ -111,17 +113,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 16 consecutive accumulator columns of this thread's lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
 // 8 consecutive accumulator columns of this thread's lane
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
@@ -132,19 +123,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// N accumulator columns from taddr on (N a multiple of 16, up to 32)
-template <int N>
-__device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[N]) {
-  static_assert(N % 16 == 0 && N <= 32, "row chunk");
-  float t[16];
-#pragma unroll
-  for (int c = 0; c < N / 16; ++c) {
-    tmem_ld16(taddr + 16 * c, t);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[16 * c + j] = t[j];
-  }
-}
 
 // Writes row r (KC chunks of 4 values) of a K-major hi|lo operand pair:
 // x[k] - shift for k < LEN, zero beyond.

@@ -376,6 +376,11 @@ class Batch:
     def autotune(self, cache_path=None, trials=0):
         fedbm_batch_autotune(self.h, cache_path, trials)
 
+    def set_tensor_cores(self, group, on=1):
+        """Switch one kernel group to the tensor-core form (on=1) or back to the
+        FMA form with automatic tiles (on=0)."""
+        fedbm_batch_set_tensor_cores(self.h, group, on)
+
     def close(self):
         if self.h is not None and self.h.value:
             fedbm_batch_destroy(self.h)
