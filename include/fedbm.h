@@ -222,8 +222,8 @@ int fedbm_info(const fedbm_solver* s, fedbm_info_t* info);
 
 /* ---- batched form -------------------------------------------------------- */
 /* Many independent cases (each its own mesh, Kn, wall speeds, time step) that
- * advance together (SURVEY batched form; the paper's Couette and cavity cases
- * of Sec. III).  Cases with the same degree, velocity set, precision,
+ * advance together (for example sweeps over the paper's Couette and cavity
+ * cases of Sec. III).  Cases with the same degree, velocity set, precision,
  * reduction, collision switch, beta and tile parameters form one group: their
  * element lists are concatenated and one stage-kernel launch per RK stage
  * covers them all (per-element time step and 1/tau, per-case wall slots);
