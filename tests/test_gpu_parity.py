@@ -182,14 +182,18 @@ def test_deviation_forms_l2_error(prec, red, tol):
     assert e_rho < tol and e_u < tol * 10, (e_rho, e_u)
 
 
-def test_full_size_cavity_nc16_sampled_two_stages():
+@pytest.mark.parametrize("tc", [1, -1])
+def test_full_size_cavity_nc16_sampled_two_stages(tc):
     """Cavity Kn=1, 64x64x2, p=4, NC 16x16 (31.5M DOF) in the benchmark's
-    launch configuration: stages 0 and 1 on the GPU, compared on sampled
-    elements with the oracle evaluated on just those elements."""
+    launch configurations (the tensor-core form, and the FMA form with the
+    autotuner's usual tile of one element and 128 threads): stages 0 and 1 on
+    the GPU, compared on sampled elements with the oracle evaluated on just
+    those elements."""
     c = cases.cavity(64, 64, 4, velset=("nc", 16), kn=1.0, U=0.1)
     pr = cases.oracle_problem(c)
     f0 = cases.initial_state(pr, amp=1e-2, seed=7)
-    s = cases.solver(c, "fp32")
+    s = cases.solver(c, "fp32", tc=tc) if tc == 1 else cases.solver(c, "fp32", epc=1, tpb=128, stages=1)
+    assert s.info.tensor_cores == (1 if tc == 1 else 0)
     s.set_state(f0)
     s.stage(0)
     f1_gpu = s.state()
