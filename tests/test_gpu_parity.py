@@ -225,3 +225,33 @@ def test_largest_velocity_sets_fp32(vs, p, sqrt2):
     pr, s, f0, f_gpu, f_or = _run_pair(c, 2, "fp32", amp=1e-2)
     assert s.info.Q == vs[1] ** 2 and s.info.Q_padded % 8 == 0
     assert cases.rel_max_err(f_gpu, f_or) < fp32_tol(pr, 10)
+
+
+@pytest.mark.parametrize("tc", [1, -1])
+def test_full_size_cavity_nc16_bf16_sampled_two_stages(tc):
+    """The BF16 deviation form of the same 31.5M-DOF cavity (the benchmark's
+    BF16 form) in both kernel forms: stages 0 and 1, compared on sampled
+    elements against the FP64 oracle within the 16-bit storage bound (12 u of
+    w times the element's largest deviation, u = 2^-8)."""
+    c = cases.cavity(64, 64, 4, velset=("nc", 16), kn=1.0, U=0.1)
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=1e-2, seed=8)
+    s = cases.solver(c, "bf16", tc=tc)
+    assert s.info.tensor_cores == (1 if tc == 1 else 0)
+    s.set_state(f0)
+    s.stage(0)
+    s.stage(1)
+    f2_gpu = s.state()
+    rng = np.random.default_rng(1)
+    K = pr.K
+    sample = np.unique(np.concatenate([[0, 1, K - 2, K - 1], rng.choice(K, 28, replace=False)]))
+    ring = np.unique(np.concatenate([sample, pr.nbr_elem[sample][pr.nbr_elem[sample] >= 0]]))
+    f1_ring, r1_ring = pr.lsrk_stage(0, f0, np.zeros((len(ring), pr.Np, pr.Q)), ring)
+    f1 = f0.copy()
+    f1[ring] = f1_ring
+    r1 = np.zeros_like(f0)
+    r1[ring] = r1_ring
+    f2_s, _ = pr.lsrk_stage(1, f1, r1[sample], sample)
+    w = pr.w[None, None, :]
+    md = np.abs(f2_s / w - 1.0).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(f2_gpu[sample] - f2_s) / (w * md)).max() < 12 * 2.0 ** -8
