@@ -255,3 +255,32 @@ def test_full_size_cavity_nc16_bf16_sampled_two_stages(tc):
     w = pr.w[None, None, :]
     md = np.abs(f2_s / w - 1.0).max(axis=(1, 2))[:, None, None]
     assert (np.abs(f2_gpu[sample] - f2_s) / (w * md)).max() < 12 * 2.0 ** -8
+
+
+def test_full_size_couette_p5_gh16_sampled_two_stages():
+    """Couette Kn=1, 256x256x2, p=5, GH D2Q16 (44M DOF, the convergence sweep's
+    largest case) in its launch configuration: stages 0 and 1 on sampled
+    elements, including both walls and the periodic seam."""
+    c = cases.couette(256, 256, 5, velset=("gh", 4), kn=1.0, U=0.1)
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=1e-2, seed=9)
+    s = cases.solver(c, "fp32")
+    s.set_state(f0)
+    s.stage(0)
+    f1_gpu = s.state()
+    s.stage(1)
+    f2_gpu = s.state()
+    rng = np.random.default_rng(2)
+    K = pr.K
+    edges = [0, 1, 2 * 255, 2 * 255 + 1, K - 2, K - 1, K - 512, K - 511]  # walls and the periodic seam
+    sample = np.unique(np.concatenate([edges, rng.choice(K, 40, replace=False)]))
+    ring = np.unique(np.concatenate([sample, pr.nbr_elem[sample][pr.nbr_elem[sample] >= 0]]))
+    f1_ring, r1_ring = pr.lsrk_stage(0, f0, np.zeros((len(ring), pr.Np, pr.Q)), ring)
+    f1 = f0.copy()
+    f1[ring] = f1_ring
+    r1 = np.zeros_like(f0)
+    r1[ring] = r1_ring
+    f2_s, _ = pr.lsrk_stage(1, f1, r1[sample], sample)
+    tol = fp32_tol(pr, 2) * np.abs(f0).max()
+    assert np.abs(f1_gpu[sample] - f1[sample]).max() <= tol
+    assert np.abs(f2_gpu[sample] - f2_s).max() <= tol
