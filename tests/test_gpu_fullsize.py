@@ -1,0 +1,60 @@
+"""Full-size checks of the benchmark configurations that the other parity
+tests only cover on reduced meshes: the 256-case batch (about 1.6G DOF) and
+the Kn = 8 BF16 cavity (128x128x2, p = 3, NC 32x32, 335M DOF)."""
+import numpy as np
+import pytest
+
+import bench
+from oracle import dg
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+
+def test_full_batch256_sampled_cases_bitwise_as_single_solvers():
+    """One step of the whole seeded 256-case batch; sampled cases (both kinds,
+    both velocity sets, several degrees) equal single solvers bit for bit."""
+    w = bench.WORKLOADS["batch256_couette_cavity_fp32"]
+    cs = bench.batch_case_list(w)
+    b = bench.make_batch(cs, 0)
+    for i in range(len(cs)):
+        b.set_equilibrium(i, 1.0, 0.0, 0.0, 1e-3, 201213487 + i)
+    b.step(1)
+    picks = sorted({0, 1, 63, 127, 128, 129, 200, 255})
+    for i in picks:
+        s = bench.make_solver(cs[i], 0)
+        s.set_equilibrium(1.0, 0.0, 0.0, 1e-3, 201213487 + i)
+        s.step(1)
+        assert np.array_equal(s.state(), b.state(i)), (i, cs[i])
+        s.close()
+    b.close()
+
+
+def test_full_size_cavity_kn8_bf16_stage0_sampled():
+    """The 335M-DOF BF16 cavity in its default launch configuration: the
+    device-generated initial state (the same SplitMix64 perturbation as the
+    oracle's) and one stage, compared on sampled elements with the oracle
+    within the 16-bit storage bound."""
+    import torch
+
+    c = cases.cavity(128, 128, 3, velset=("nc", 32), kn=8.0, U=0.1)
+    pr = cases.oracle_problem(c)
+    amp, seed = 1e-2, 77
+    s = cases.solver(c, "bf16", "fp64")
+    s.set_equilibrium(1.0, 0.0, 0.0, amp, seed)
+    s.stage(0)
+    K, Np, Q = s.shape
+    f_dev = torch.empty((K, Np, Q), dtype=torch.float64, device="cuda")
+    from paper_2012_13487_gb300 import fedbm as fb
+    fb.fedbm_get_state(s.h, f_dev, True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    sample = np.unique(np.concatenate([[0, 1, 2 * 127, K - 2, K - 1], rng.choice(K, 19, replace=False)]))
+    f1_gpu = f_dev[torch.as_tensor(sample, device="cuda")].cpu().numpy()
+    del f_dev
+    f0 = cases.initial_state(pr, amp=amp, seed=seed)
+    f1_s, _ = pr.lsrk_stage(0, f0, np.zeros((len(sample), Np, Q)), sample)
+    del f0
+    w = pr.w[None, None, :]
+    md = np.abs(f1_s / w - 1.0).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(f1_gpu - f1_s) / (w * md)).max() < 12 * 2.0 ** -8
