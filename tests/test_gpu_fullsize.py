@@ -1,6 +1,7 @@
 """Full-size checks of the benchmark configurations that the other parity
-tests only cover on reduced meshes: the 256-case batch (about 1.6G DOF) and
-the Kn = 8 BF16 cavity (128x128x2, p = 3, NC 32x32, 335M DOF)."""
+tests only cover on reduced meshes: the 256-case batch (about 1.6G DOF),
+the Kn = 8 BF16 cavity (128x128x2, p = 3, NC 32x32, 335M DOF) and the
+GH D2Q16 cavity (64x64x2, p = 4, 1.97M DOF)."""
 import numpy as np
 import pytest
 
@@ -58,3 +59,20 @@ def test_full_size_cavity_kn8_bf16_stage0_sampled():
     w = pr.w[None, None, :]
     md = np.abs(f1_s / w - 1.0).max(axis=(1, 2))[:, None, None]
     assert (np.abs(f1_gpu - f1_s) / (w * md)).max() < 12 * 2.0 ** -8
+
+
+
+@pytest.mark.parametrize("tc", [1, -1], ids=["tensor-cores", "fma"])
+def test_full_size_cavity_gh16_three_steps(tc):
+    """Cavity Kn=1, 64x64x2, p=4, GH D2Q16 (1.97M DOF): three whole LSRK(5,4)
+    steps in both kernel forms, compared with the oracle on every value."""
+    c = cases.cavity(64, 64, 4, velset=("gh", 4), kn=1.0, U=0.1)
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=1e-2, seed=12)
+    s = cases.solver(c, "fp32", tc=tc)
+    s.set_state(f0)
+    s.step(3)
+    err = cases.rel_max_err(s.state(), pr.run(f0, 3))
+    tol = 4.0 * pr.Np * 2.0 ** -24 * np.sqrt(15) + 2.0 ** -24
+    assert err <= tol, (err, tol)
+    s.close()
