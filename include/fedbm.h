@@ -111,8 +111,8 @@ typedef struct fedbm_params {
                               the next tile while computing one (0 = auto = 1) */
   int32_t tensor_cores;  /* stage-kernel form: 0 = tensor cores (tcgen05 TF32
                             MMAs for the Dr, Ds, LIFT contractions) for FP32
-                            and BF16 state with 128 or 256 padded velocities
-                            at degree <= 4 when no tile is given above, else
+                            state with 128 or 256 padded velocities at
+                            degree <= 4 when no tile is given above, else
                             the FMA kernel;
                             1 = tensor cores required (EINVAL where the form
                             has none); -1 = FMA kernel only.  The tensor-core

@@ -883,14 +883,15 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
          for (Group& g : b->groups) {
            const int epc = g.epc, tpb = g.tpb, st = g.nstages;
            if ((r = build_group(*b, g)) != FEDBM_OK) return r;
-           // default: tensor cores for FP32 and BF16 state with 128 or 256
-           // padded velocities up to degree 4 (measured no slower than the FMA
-           // kernel there); the FP16 form's rescaling sweep, the eight
-           // dependent MMA rounds of 1024 velocities, the few stacked tiles of
-           // small 16-velocity meshes and the two CTAs per SM of degree 5 make
-           // the FMA kernel the faster one elsewhere
+           // default: tensor cores for FP32 state with 128 or 256 padded
+           // velocities up to degree 4 (measured within a few per cent of the
+           // FMA kernel there); the 16-bit forms (the FMA kernel encodes BF16
+           // in its update and keeps more CTAs per SM), the eight dependent
+           // MMA rounds of 1024 velocities, the few stacked tiles of small
+           // 16-velocity meshes and the two CTAs per SM of degree 5 make the
+           // FMA kernel the faster one elsewhere
            const bool want_tc = g.tc_mode > 0 || (g.tc_mode == 0 && epc == 0 && tpb == 0 && st == 0 &&
-                                                   g.store != kStoreF16 && g.Qp >= 128 && g.Qp <= 256 &&
+                                                   g.store == kStoreF32 && g.Qp >= 128 && g.Qp <= 256 &&
                                                    g.p <= 4 && tc_available(g));
            if (want_tc) {
              if ((r = configure_tc(*b, g)) != FEDBM_OK) return r;

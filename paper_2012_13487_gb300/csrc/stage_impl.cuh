@@ -31,9 +31,10 @@
 
 // Largest degree whose 16-bit forms take two velocities per thread (and the
 // FP32 state too when FEDBM_VPT2_FP32_STATE is 1); FEDBM_PACKED_FMA = 1 runs
-// the two velocities' contractions as packed FP32 pairs.
+// the two velocities' contractions as packed FP32 pairs.  Measured on the BF16
+// cavities: two velocities per thread are faster at degree 3, one at degree 4.
 #ifndef FEDBM_VPT2_MAX_P
-#define FEDBM_VPT2_MAX_P 4
+#define FEDBM_VPT2_MAX_P 3
 #endif
 #ifndef FEDBM_VPT2_FP32_STATE
 #define FEDBM_VPT2_FP32_STATE 0
@@ -372,8 +373,18 @@ __device__ __forceinline__ R collision(const R* mm, R ex, R ey, R w, R f, R inv_
   return fma(w, feq, -inv_tau * f);
 }
 
+// Deviation form whose 16-bit format has FP32's exponent range (BF16): a
+// power-of-two element scale changes neither the rounding of q nor the decoded
+// f = w (1 + s q), so the element keeps the scale it was encoded with and the
+// new state is encoded where it is computed.  FP16 (|q| < 2^15) must rescale.
+template <class ST>
+__host__ __device__ constexpr bool keeps_scale() {
+  if constexpr (ST::dev) return ST::qmax_log2 == 0;
+  else return false;
+}
+
 // Adjacent velocities handled by one thread in phase 4: two for the
-// specialised 16-bit-state kernels up to degree 4 (each operator constant then
+// specialised 16-bit-state kernels up to degree 3 (each operator constant then
 // feeds two FMAs and the per-item set-up is shared), else one.
 template <class ST, int QT>
 __host__ __device__ constexpr int items_vpt() {
@@ -389,8 +400,9 @@ struct alignas(N * sizeof(T)) Vec {
 
 // Phase 4: residual, 2N-storage update and write-back of every (element,
 // velocity) value of the tile; each thread owns VPT adjacent velocities of one
-// element.  Plain forms update f in place in shared memory; deviation forms
-// only track max |f/w - 1| per element (the encoding pass recomputes f).
+// element.  Plain forms and BF16 (kept element scale) update f in place in
+// shared memory; FP16 only tracks max |f/w - 1| per element (the encoding pass
+// recomputes f with the new scale).
 template <class ST, int QT, int VPT>
 __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
                                             StageSmem<typename ST::R, typename ST::S>& sm, int64_t k0, int ne,
@@ -405,6 +417,8 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
   const R rkA = a.rkA, rkB = a.rkB, ab = a.ab;
   const bool third = a.eq_order == 3;
   constexpr bool kPacked = FEDBM_PACKED_FMA && sizeof(R) == 4 && VPT == 2;
+  constexpr bool kKeep = keeps_scale<ST>();
+  constexpr bool kTrack = ST::dev && !kKeep;
   for (int item = tid; item < ne * Qv; item += nth) {
     const int e = item / Qv;
     const int i = (item - e * Qv) * VPT;
@@ -476,7 +490,7 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
     if constexpr (ST::dev) {
       const RV iw = *reinterpret_cast<const RV*>(a.vel + kVelInvW * Qp + i);
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) invw[v] = iw.v[v];
+      for (int v = 0; v < VPT; ++v) invw[v] = iw.v[v] * (kKeep ? R(1) / R(sm.scale[e]) : R(1));
     }
 #pragma unroll
     for (int n = 0; n < NP; ++n) {
@@ -527,16 +541,18 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
         if (read_res) r = fma(rkA, rold.v[v], r);
         rr.v[v] = r;
         const R fnew = new_f<ST>(fr[v][n], rkB, r);
-        if constexpr (ST::dev) {
+        if constexpr (kTrack) {
           dloc = fmaxf(dloc, fabsf((fnew - wv.v[v]) * invw[v]));
+        } else if constexpr (kKeep) {
+          fnew_s.v[v] = ST::from_r((fnew - wv.v[v]) * invw[v]);
         } else {
           fnew_s.v[v] = S(fnew);
         }
       }
       *reinterpret_cast<RV*>(rrow + n * Qp) = rr;
-      if constexpr (!ST::dev) *reinterpret_cast<SV*>(frow + n * Qp) = fnew_s;
+      if constexpr (!kTrack) *reinterpret_cast<SV*>(frow + n * Qp) = fnew_s;
     }
-    if constexpr (ST::dev) {
+    if constexpr (kTrack) {
       if (e != emax) {
         if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
         emax = e;
@@ -713,8 +729,11 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
     int emax = -1;
     item_update<ST, QT, items_vpt<ST, QT>()>(a, sm, k0, ne, read_res, dmax, emax);
 
-    // ---- 5. deviation forms: new per-element scale, encoding in place ------------
-    if constexpr (ST::dev) {
+    // ---- 5. deviation forms: the kept scale (BF16), or the new per-element
+    // scale and the encoding in place (FP16) ------------------------------------
+    if constexpr (keeps_scale<ST>()) {
+      for (int e = tid; e < ne; e += nth) a.scale_out[k0 + e] = sm.scale[e];
+    } else if constexpr (ST::dev) {
       if (emax >= 0) atomicMax(&sm.dmax[emax], __float_as_uint(dmax));
       __syncthreads();
       for (int e = tid; e < ne; e += nth) {

@@ -143,13 +143,6 @@ __device__ __forceinline__ void put_row(float* hi, float* lo, int r, const float
   }
 }
 
-// deviation form whose 16-bit format has FP32's exponent range (BF16)
-template <class ST>
-__host__ __device__ constexpr bool keeps_scale() {
-  if constexpr (ST::dev) return ST::qmax_log2 == 0;
-  else return false;
-}
-
 }  // namespace tc
 
 // Bulk copies of one tile's state and geometry (warp 0): elements k0 ..
@@ -193,7 +186,7 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
   // keeps its scale and the new state is encoded straight from registers.
   // FP16 (|q| < 2^15) needs the new scale of the element's largest deviation,
   // found after every velocity is done, and a second encoding sweep.
-  constexpr bool kKeepScale = tc::keeps_scale<ST>();
+  constexpr bool kKeepScale = keeps_scale<ST>();
   constexpr bool kRescale = ST::dev && !kKeepScale;
   static_assert(QT % kTcThreads == 0 || kTcThreads % QT == 0, "whole passes or whole stacked elements");
   constexpr int EPT = elems_per_tile(QT);                       // elements per tile
@@ -540,7 +533,7 @@ cudaError_t with_tc_kernel(int store_kind, int Qp, Fn fn) {
   if constexpr (P <= kTcMaxP) {
     auto by_q = [&](auto st) -> cudaError_t {
       using ST = decltype(st);
-      if constexpr (!ST::dev || tc::keeps_scale<ST>())
+      if constexpr (!ST::dev || keeps_scale<ST>())
         if (Qp == 16) return fn(stage_kernel_tc<ST, 16>);
       if (Qp == 256) return fn(stage_kernel_tc<ST, 256>);
       if (Qp == 128) return fn(stage_kernel_tc<ST, 128>);

@@ -59,10 +59,11 @@ def test_tc_1024_velocities_cavity_kn8(p):
 def test_tc_default_selection_and_rejection():
     from paper_2012_13487_gb300 import fedbm as fb
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32").info.tensor_cores == 1
-    # explicit FMA tiles, other velocity counts, FP64 state, degree >= 5: FMA form
+    # explicit FMA tiles, other velocity counts, 16-bit or FP64 state, degree >= 5: FMA form
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32", epc=2).info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("gh", 5)), "fp32").info.tensor_cores == 0
-    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "bf16").info.tensor_cores == 1
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "bf16").info.tensor_cores == 0
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "bf16", tc=1).info.tensor_cores == 1
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp64").info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp16").info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp16", tc=1).info.tensor_cores == 1
