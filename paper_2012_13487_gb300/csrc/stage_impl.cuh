@@ -64,10 +64,25 @@ static __constant__ double c_ops64[OPS_N];
 // every FP32 coefficient twice, as the broadcast operand of a packed FMA
 static __constant__ unsigned long long c_ops32x2[OPS_N];
 
+#include "ops_tables.inc"
+
 template <typename R>
 __device__ __forceinline__ R opv(int idx);
+#ifdef FEDBM_OPS32_TABLE
+// FP32 operators of this degree (<= 4) as a compile-time table: the operators
+// depend only on the degree, and with the node loops unrolled every Dr, Ds and
+// LIFT entry becomes an instruction immediate instead of a constant-memory
+// load.  The table holds the runtime upload's values (a CPU test checks it).
+template <>
+__device__ __forceinline__ float opv<float>(int idx) {
+  constexpr float t[] = {FEDBM_OPS32_TABLE};
+  static_assert(sizeof(t) / sizeof(t[0]) == OPS_N, "operator table of another degree");
+  return t[idx];
+}
+#else
 template <>
 __device__ __forceinline__ float opv<float>(int idx) { return c_ops32[idx]; }
+#endif
 template <>
 __device__ __forceinline__ double opv<double>(int idx) { return c_ops64[idx]; }
 
