@@ -884,8 +884,9 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
            const int epc = g.epc, tpb = g.tpb, st = g.nstages;
            if ((r = build_group(*b, g)) != FEDBM_OK) return r;
            // default: tensor cores for FP32 state with 128 or 256 padded
-           // velocities up to degree 4 (measured within a few per cent of the
-           // FMA kernel there); the 16-bit forms (the FMA kernel encodes BF16
+           // velocities up to degree 4 (the autotuner times both forms; with
+           // its compile-time operator tables the FMA kernel is now the faster
+           // one there too, 2.52e11 vs 2.04e11-2.20e11 DOF-stage/s); the 16-bit forms (the FMA kernel encodes BF16
            // in its update and keeps more CTAs per SM), the eight dependent
            // MMA rounds of 1024 velocities, the few stacked tiles of small
            // 16-velocity meshes and the two CTAs per SM of degree 5 make the
