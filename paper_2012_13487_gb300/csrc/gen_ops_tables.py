@@ -1,9 +1,11 @@
 """Writes ops_tables.inc: the FP32 Dr, Ds and LIFT operators of degrees 0..4
 as compile-time tables for the FMA stage kernel.
 
-The operators depend only on the degree (Warburton's warp & blend nodes on the
-reference triangle, Sec. II.B), so the FP32 kernels can take them as
-instruction immediates instead of loading them from constant memory.  The
+The nodal Lagrange basis of Sec. II.B.1 lives on one reference triangle, so
+Dr, Ds and LIFT depend only on the degree (and on the node set, which the paper
+leaves open: warp & blend nodes with alpha = 0 here).  The FP32 kernels can
+therefore take them as instruction immediates instead of loading them from
+constant memory.  The
 values are the library's own operators (``fedbm_ref_operators``) rounded to
 FP32 exactly as the runtime upload rounds them; a CPU test checks that the
 committed file still matches.  Degrees 5 and 6 (441 and 784 entries per
