@@ -296,6 +296,89 @@ def oracle_sample(w, seconds, nelem=512, min_stages=1, max_stages=10 ** 9):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+ORACLE_ERROR_SCRIPT = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle import dg
+from paper_2012_13487_gb300 import inputs
+w = json.loads(%(w)r)
+kind, n = w["vel"]
+if w["kind"] == "cavity":
+    bc = ("diffuse",) * 4; wall = ((0, 0), (0, 0), (w["speed"], 0), (0, 0))
+else:
+    bc = ("diffuse", "periodic", "diffuse", "periodic"); wall = ((-w["speed"], 0), (0, 0), (w["speed"], 0), (0, 0))
+t0 = time.perf_counter()
+pr = dg.Problem(w["nx"], w["ny"], w["p"], velset=(kind, n), kn=w["kn"], bc=bc, wall_u=wall)
+f = pr.equilibrium_state(amp=%(amp)r, u=inputs.perturbation(%(seed)d, pr.K, pr.Np, pr.Q))
+f = pr.run(f, %(steps)d)
+orho, oux, ouy = pr.nodal_moments(f)
+zero = lambda x, y: 0 * x
+out = {"oracle_seconds": time.perf_counter() - t0}
+for tag, path in json.loads(%(gpu)r).items():
+    g = np.load(path)
+    e_rho = pr.l2_error(g["rho"] - orho, zero)
+    e_u = np.hypot(pr.l2_error(g["ux"] - oux, zero), pr.l2_error(g["uy"] - ouy, zero)) / w["speed"]
+    out[tag] = {"l2_rho": float(e_rho), "l2_u_over_U": float(e_u),
+                "max_abs_u_over_U": float(max(np.abs(g["ux"] - oux).max(), np.abs(g["uy"] - ouy).max()) / w["speed"]),
+                "max_abs_rho": float(np.abs(g["rho"] - orho).max())}
+print(json.dumps(out))
+"""
+
+ERROR_STEPS = 2
+ERROR_AMP = 1e-3
+ERROR_SEED = 201213487
+
+
+def error_copy(w):
+    """The mesh copy on which a workload's error against the FP64 oracle is
+    taken: the workload itself when it has at most 32 x 32 cells, else its
+    32 x 32 x 2 copy (the size the precision configuration names) with the
+    same degree, velocity set, Kn and wall speed."""
+    c = dict(w)
+    c["nx"], c["ny"] = min(w["nx"], 32), min(w["ny"], 32)
+    return c
+
+
+def gpu_error_moments(w, forms, st, tmpdir):
+    """Moments of each (precision, reduction) form after ERROR_STEPS steps on the
+    error copy, from the seeded perturbed rest state drawn by the library."""
+    import numpy as np
+    import torch
+    c = error_copy(w)
+    paths = {}
+    for prec, red in forms:
+        wc = dict(c, precision=prec, reduction=red)
+        s = make_solver(wc, st.cuda_stream)
+        s.set_equilibrium(1.0, 0.0, 0.0, ERROR_AMP, ERROR_SEED)
+        s.step(ERROR_STEPS)
+        rho, ux, uy = s.moments()
+        torch.cuda.synchronize()
+        s.close()
+        path = os.path.join(tmpdir, "%s_%s.npz" % (prec, red))
+        np.savez(path, rho=rho, ux=ux, uy=uy)
+        paths["%s/%s" % (prec, red)] = path
+    return c, paths
+
+
+def oracle_errors(c, paths):
+    """L2 errors of rho and u (over the wall or lid speed) of the GPU forms
+    against the FP64 oracle on the same copy and steps (oracle leg: a CPU
+    subprocess with no GPU visible)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    script = ORACLE_ERROR_SCRIPT % dict(root=ROOT, w=json.dumps(c), amp=ERROR_AMP, seed=ERROR_SEED,
+                                        steps=ERROR_STEPS, gpu=json.dumps(paths))
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle error run failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["copy"] = "%dx%dx2 triangles, p=%d, %s, Kn=%g, speed %g; %d LSRK(5,4) steps from the rest state " \
+                  "x (1 + %g u), u SplitMix64 seed %d" % (c["nx"], c["ny"], c["p"], c["vel"], c["kn"], c["speed"],
+                                                           ERROR_STEPS, ERROR_AMP, ERROR_SEED)
+    return out
+
+
 # ---------------------------------------------------------------- arms
 def max_over_ranks(x, dist, device):
     """The largest x over all ranks (a job's time is its slowest rank's); x
@@ -381,8 +464,75 @@ def run_reference(args, w, name):
     print(json.dumps(line), flush=True)
 
 
+REPEATS = 5
+DTYPE = {"fp32": "f32", "fp64": "f64", "bf16": "bf16-state/f32", "fp16": "f16-state/f32"}
+
+
+def timed_repeats(step, stream, steps, repeats, barrier, dist):
+    """`repeats` timed regions of `steps` steps each: barrier + synchronize on
+    both sides, CUDA events on the launching stream, the max over ranks of
+    each region.  Returns the milliseconds of every region."""
+    import torch
+    out = []
+    for _ in range(repeats):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        out.append(max_over_ranks(e0.elapsed_time(e1), dist, "cuda"))
+    return out
+
+
+def spread(ms, steps):
+    """Median and spread of repeated timed regions, per step."""
+    per = [m / steps for m in ms]
+    return {"n": len(per), "ms_per_step_median": statistics.median(per), "ms_per_step_min": min(per),
+            "ms_per_step_max": max(per), "spread_pct": 100.0 * (max(per) - min(per)) / statistics.median(per)}
+
+
+def roofline_of(dof, prec, ms_per_step, kernel, traffic=None):
+    """Roofline of the stage kernel: algorithmic bytes of one launch over the
+    average launch time (five launches per step, back to back in a graph)."""
+    alg = dof * algorithmic_bytes_per_dof_step(prec)
+    achieved = alg / (ms_per_step / 1e3) / 1e9
+    peak, peak_kind = hbm_peak()
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "traffic": traffic,
+            "algorithmic_bytes_per_dof_step": algorithmic_bytes_per_dof_step(prec),
+            "algorithmic_bytes_per_launch": alg / 5.0, "kernel": kernel}
+
+
+def measure_form(w, st, steps, warmup, tune, repeats=3):
+    """Throughput of one (workload, precision, reduction) form: the FMA kernel
+    by default, autotuned over both kernel forms when `tune`."""
+    s = make_solver(w, st.cuda_stream)
+    s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+    if tune:
+        s.autotune(None, 10)
+    K, Np, Q = dims(w)
+    dof = K * Np * Q
+    s.step(warmup)
+    ms = timed_repeats(s.step, st, steps, repeats, lambda: None, None)
+    sp = spread(ms, steps)
+    info = s.info
+    s.mass()
+    s.close()
+    kern = "stage_kernel_tc" if info.tensor_cores else "stage_kernel"
+    return {"value": dof * 5 / (sp["ms_per_step_median"] / 1e3), "unit": "DOF-stage/s", "workload": w["desc"],
+            "precision": w["precision"], "reduction": w.get("reduction", "default"), "dof": dof,
+            "steps": steps, "repeats": sp,
+            "tile": {"elems_per_cta": info.elems_per_cta, "threads_per_cta": info.threads_per_cta,
+                     "pipeline_stages": info.pipeline_stages, "grid": info.grid,
+                     "tensor_cores": info.tensor_cores},
+            "roofline": roofline_of(dof, w["precision"], sp["ms_per_step_median"], kern)}
+
+
 def run_ours(args, w, name):
-    import numpy as np
     import torch
 
     world, rank, local = dist_setup()
@@ -412,27 +562,15 @@ def run_ours(args, w, name):
 
     sampler = ClockSampler(local)
     sampler.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    s.step(args.steps)
-    e1.record(st)
-    torch.cuda.synchronize()
-    barrier()
-    ms = e0.elapsed_time(e1)
+    ms_list = timed_repeats(s.step, st, args.steps, args.repeats, barrier, dist)
     clocks = sampler.stop()
     mass = s.mass()   # also raises on NaN / rho <= 0
-    ms = max_over_ranks(ms, dist, "cuda")
-    secs = ms / 1e3
+    sp = spread(ms_list, args.steps)
+    ms_step = sp["ms_per_step_median"]
+    secs = ms_step * args.steps / 1e3
     value = job_throughput(world, dof * 5 * args.steps, secs)
-
-    # roofline of the stage kernel: algorithmic bytes / average launch time
-    alg_bytes_step = dof * algorithmic_bytes_per_dof_step(w["precision"])
-    achieved = alg_bytes_step * args.steps / secs / 1e9
-    peak, peak_kind = hbm_peak()
-    traffic = recorded_traffic(name)
+    kern = ("stage_kernel_tc" if s.info.tensor_cores else "stage_kernel") + " (5 launches per step; average over the mix)"
+    roof = roofline_of(dof, w["precision"], ms_step, kern, recorded_traffic(name))
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(3, min(args.steps, 20))
@@ -500,8 +638,14 @@ def run_ours(args, w, name):
     # reproduce the serial read-out bit for bit
     if not torch.equal(rho, rho_serial):
         raise RuntimeError("pipelined end-to-end read-out differs from the serial one")
+    tile = {"elems_per_cta": s.info.elems_per_cta, "threads_per_cta": s.info.threads_per_cta,
+            "pipeline_stages": s.info.pipeline_stages, "grid": s.info.grid,
+            "tensor_cores": s.info.tensor_cores}
+    s.close()
 
     cpu = None
+    error = None
+    forms = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out = oracle_sample(w, seconds=args.cpu_seconds)
         cpu = {"value": out["dof_stages"] / out["seconds"], "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
@@ -509,44 +653,26 @@ def run_ours(args, w, name):
                          "%d-element mesh, single thread, %.1f s" % (out["stages"], out["elements"],
                                                                      out["dof_stages"] // out["stages"],
                                                                      out["K"], out["seconds"])}
-    forms = None
+    if rank == 0 and world == 1 and not args.no_error:
+        with tempfile.TemporaryDirectory() as td:
+            copy, paths = gpu_error_moments(w, [(w["precision"], w.get("reduction", "default"))], st, td)
+            error = oracle_errors(copy, paths)
     if rank == 0 and world == 1 and not args.no_forms and name == DEFAULT_WORKLOAD:
-        # the three forms of the metric: FP32 state (this line), BF16 deviation
-        # state on the same mesh, and the seeded 256-case batch
-        wb = dict(w, precision="bf16", desc=w["desc"].replace("FP32", "BF16 deviation state"))
-        if not args.no_tune:
-            sb = pick_form(wb, st, torch)
-        else:
-            sb = make_solver(wb, st.cuda_stream)
-            sb.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
-        ms_b = time_steps(sb.step, st, max(1, args.steps // 2), args.warmup)
-        sb.close()
-        bat = measure_batch(WORKLOADS["batch256_couette_cavity_fp32"], st, 10, 3, 2, not args.no_tune)
-        forms = {"fp32": {"value": value, "workload": w["desc"]},
-                 "bf16_state": {"value": dof * 5 * max(1, args.steps // 2) / (ms_b / 1e3), "workload": wb["desc"],
-                                "algorithmic_bytes_per_dof_step": algorithmic_bytes_per_dof_step("bf16")},
-                 "batched": dict(bat, workload=WORKLOADS["batch256_couette_cavity_fp32"]["desc"]),
-                 "unit": "DOF-stage/s"}
+        forms = measure_forms(args, w, st, value, roof, error)
     if rank == 0:
         line = {
             "metric": "DOF-stage updates/s", "value": value, "unit": "DOF-stage/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-state/f32", "fp16": "f16-state/f32"}[w["precision"]],
-            "data": "synthetic",
+            "dtype": DTYPE[w["precision"]], "data": "synthetic",
             "config": {"workload": w["desc"], "name": name, "K": K, "Np": Np, "Q": Q, "dof": dof,
-                       "tile": {"elems_per_cta": s.info.elems_per_cta, "threads_per_cta": s.info.threads_per_cta,
-                                "pipeline_stages": s.info.pipeline_stages, "grid": s.info.grid,
-                                "tensor_cores": s.info.tensor_cores},
+                       "reduction": w.get("reduction", "default"), "tile": tile,
                        "l2": "inputs larger than L2 (state x2 + residual = %.0f MB), no flush" %
                              (dof * (2 * STATE_BYTES[w["precision"]] + RES_BYTES[w["precision"]]) / 1e6),
                        "parallelism": "replicas x%d" % world},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": traffic,
-                         "algorithmic_bytes_per_dof_step": algorithmic_bytes_per_dof_step(w["precision"]),
-                         "kernel": ("stage_kernel_tc" if s.info.tensor_cores else "stage_kernel")
-                                   + " (5 launches per step; average over the mix)"},
+            "repeats": sp,
+            "roofline": roof,
+            "error": error,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "DOF-stage/s", "steps": e2e_steps,
                     "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": 3 * K * Np * 8,
@@ -555,15 +681,54 @@ def run_ours(args, w, name):
                     "serial": {"value": serial_value, "unit": "DOF-stage/s",
                                "path": "fedbm_set_state(host FP64) + fedbm_rk_step(1) + fedbm_get_moments(host), "
                                        "one step after the other"}},
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": 5 * args.steps * args.repeats,
             "clocks": clocks,
             "mass_after": mass,
             "forms": forms,
         }
         print(json.dumps(line), flush=True)
-    s.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# the other forms of the metric, each with its own roofline and error against
+# the oracle: (key, workload, precision, reduction)
+FORMS = [
+    ("fp32_red_fp64", DEFAULT_WORKLOAD, "fp32", "fp64"),
+    ("fp32_red_comp", DEFAULT_WORKLOAD, "fp32", "comp"),
+    ("bf16_state", DEFAULT_WORKLOAD, "bf16", "default"),
+    ("couette_256x256x2_p5_gh16_fp32", "couette_kn1_256x256x2_p5_gh16_fp32", "fp32", "default"),
+    ("couette_256x256x2_p5_gh16_bf16", "couette_kn1_256x256x2_p5_gh16_bf16", "bf16", "default"),
+    ("cavity_kn8_128x128x2_p3_nc32_bf16_red_fp64", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "bf16", "fp64"),
+    ("cavity_kn8_128x128x2_p3_nc32_bf16_red_comp", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "bf16", "comp"),
+    ("cavity_kn8_128x128x2_p3_nc32_fp16_red_fp64", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "fp16", "fp64"),
+]
+
+
+def measure_forms(args, w, st, value, roof, error):
+    """Every form of FORMS (throughput, roofline, error on its copy) and the
+    seeded 256-case batch against a loop of single solvers."""
+    forms = {"fp32": {"value": value, "workload": w["desc"], "roofline": roof, "error": error},
+             "unit": "DOF-stage/s"}
+    steps = max(20, args.steps)
+    by_copy = {}
+    for key, wname, prec, red in FORMS:
+        wf = dict(WORKLOADS[wname], precision=prec, reduction=red)
+        wf["desc"] = "%s [%s state, %s moment sums]" % (WORKLOADS[wname]["desc"].split(", BF16")[0].split(", FP32")[0],
+                                                       prec.upper(), red)
+        forms[key] = measure_form(wf, st, steps, args.warmup, not args.no_tune)
+        by_copy.setdefault(wname, []).append((key, prec, red))
+    if not args.no_error:
+        for wname, items in by_copy.items():
+            wf = WORKLOADS[wname]
+            with tempfile.TemporaryDirectory() as td:
+                copy, paths = gpu_error_moments(wf, [(p, r) for _, p, r in items], st, td)
+                errs = oracle_errors(copy, paths)
+            for key, prec, red in items:
+                forms[key]["error"] = dict(errs["%s/%s" % (prec, red)], copy=errs["copy"])
+    bat = measure_batch(WORKLOADS["batch256_couette_cavity_fp32"], st, 10, 3, 2, not args.no_tune)
+    forms["batched"] = dict(bat, workload=WORKLOADS["batch256_couette_cavity_fp32"]["desc"])
+    return forms
 
 
 def run_batch_workload(args, w, name, st, world, rank, dist):
@@ -620,7 +785,10 @@ def main():
     ap.add_argument("--tc", type=int, default=0, choices=[-1, 0, 1],
                     help="stage-kernel form: 1 tensor cores, -1 FMA only, 0 library default")
     ap.add_argument("--no-tune", action="store_true", help="skip the tile autotuner")
-    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 and batched form measurements")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other forms (precisions, reductions, "
+                    "the p=5 Couette and Kn=8 cavity configurations, the batch)")
+    ap.add_argument("--no-error", action="store_true", help="skip the error against the oracle")
+    ap.add_argument("--repeats", type=int, default=REPEATS, help="timed regions of --steps steps (median reported)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -17,9 +17,10 @@
  *    until the next failing call on the same thread).  No C++ exception crosses
  *    the ABI.
  *  - Canonical state layout: double f[K][Np][Q], velocity index fastest.
- *    Element k = 2*(iy*nx + ix) + t of square (ix, iy); t = 0 is the triangle
- *    (A, B, C), t = 1 is (A, C, D), where A, B, C, D are the square's corners
- *    (x0,y0), (x1,y0), (x1,y1), (x0,y1); nodes are the warp & blend nodes
+ *    Structured meshes: element k = 2*(iy*nx + ix) + t of square (ix, iy);
+ *    t = 0 is the triangle (A, B, C), t = 1 is (A, C, D), where A, B, C, D are
+ *    the square's corners (x0,y0), (x1,y0), (x1,y1), (x0,y1); unstructured
+ *    meshes: element k is the caller's triangle k.  Nodes are the warp & blend nodes
  *    (alpha = 0) numbered row by row in the reference s direction; velocity
  *    i = ix*n + iy of the n x n tensor set.  Node moments use [K][Np].
  *  - Ownership: the caller owns every buffer it passes; the library never keeps
@@ -72,17 +73,36 @@ enum fedbm_reduction {
 };
 
 /* ---- descriptors -------------------------------------------------------- */
-/* Structured mesh on [0, lx] x [0, ly] (Sec. III: Cartesian cells split into two
- * triangles).  Sides: 0 -> y = 0, 1 -> x = lx, 2 -> y = ly, 3 -> x = 0.
- * Periodic sides must come in opposite pairs.  Wall velocities are tangential
- * (the component normal to the wall must be 0). */
+/* Mesh of straight-sided triangles on the rectangle [0, lx] x [0, ly].
+ * Sides: 0 -> y = 0, 1 -> x = lx, 2 -> y = ly, 3 -> x = 0.  Periodic sides must
+ * come in opposite pairs.  Wall velocities are tangential (the component
+ * normal to the wall must be 0).
+ *
+ * Structured (ntri = 0, Sec. III.A): nx x ny Cartesian cells, each split along
+ * its lower-left/upper-right diagonal into two triangles; K = 2 nx ny.
+ *
+ * Unstructured (ntri > 0, the cavity meshes of Sec. III.B): a conforming
+ * triangulation given by nvert vertices vert_xy[nvert][2] and ntri triangles
+ * tri[ntri][3] (vertex indices, counter-clockwise); element k is triangle k,
+ * face f joins its vertices f and f+1 mod 3.  The vertices must span
+ * [0, lx] x [0, ly] (lx, ly are taken from them; the lx, ly fields and nx, ny
+ * are ignored); every edge that only one triangle has must lie on a side of
+ * that rectangle, and periodic sides must carry edges with the same end-point
+ * coordinates along the side.  Both arrays are host memory, read during the
+ * call that takes the descriptor (create, or a host-only query) and not kept.
+ * Errors (EINVAL): indices out of range, a clockwise or degenerate triangle,
+ * an edge shared by more than two triangles, a boundary edge inside the
+ * rectangle, unmatched periodic edges. */
 typedef struct fedbm_mesh_desc {
-  int32_t nx, ny;        /* cells in x and y; K = 2 nx ny elements           */
+  int32_t nx, ny;        /* structured: cells in x and y; K = 2 nx ny          */
   int32_t order;         /* polynomial degree p, 0..6                         */
   int32_t bc[4];         /* enum fedbm_bc_kind per side                        */
   double  wall_ux[4];    /* wall velocity per side, units of sqrt(RT)          */
   double  wall_uy[4];
-  double  lx, ly;        /* domain size; 0 means 1                              */
+  double  lx, ly;        /* structured: domain size; 0 means 1                 */
+  int32_t nvert, ntri;   /* unstructured: vertex and triangle counts (0: structured) */
+  const double*  vert_xy; /* unstructured: [nvert][2] vertex coordinates       */
+  const int32_t* tri;     /* unstructured: [ntri][3] counter-clockwise triangles */
 } fedbm_mesh_desc;
 
 /* Velocity set (Sec. II.A.3, Table 1; Newton-Cotes grid of Sec. III.B).
@@ -109,21 +129,23 @@ typedef struct fedbm_params {
                             <= 256 (0 = auto)                                  */
   int32_t pipeline_stages; /* stage-kernel tile buffers per CTA: 1, or 2 to load
                               the next tile while computing one (0 = auto = 1) */
-  int32_t tensor_cores;  /* stage-kernel form: 0 = tensor cores (tcgen05 TF32
-                            MMAs for the Dr, Ds, LIFT contractions) for FP32
-                            state with 128 or 256 padded velocities at
-                            degree <= 4 when no tile is given above, else
-                            the FMA kernel;
-                            1 = tensor cores required (EINVAL where the form
-                            has none); -1 = FMA kernel only.  The tensor-core
+  int32_t tensor_cores;  /* stage-kernel form: 0 = the FMA kernel (the
+                            faster form on every measured shape), with the
+                            tensor-core form as one of the autotuner's
+                            candidates; 1 = tensor cores (tcgen05 TF32 MMAs
+                            for the Dr, Ds, LIFT contractions) required
+                            (EINVAL where the form has none); -1 = FMA
+                            kernel only, also for the autotuner.  The tensor-core
                             form exists at degree <= 5 for FP32, BF16 and FP16
                             state with 128, 256 or 1024 padded velocities,
                             and for FP32 and BF16 state with 16 (eight
                             elements stacked per MMA tile)                   */
   int32_t test_wait_timeout; /* test hook, keep 0: when 1, every stage kernel
                               waits for 16 bytes that never arrive, so its
-                              bounded wait (about 3 s) runs out, the kernel
-                              returns and fedbm_mass reports FEDBM_ETIMEOUT  */
+                              bounded wait (about 2 s) runs out, the kernel
+                              returns and the next synchronous read-out
+                              (fedbm_mass, or get_moments / get_state to
+                              host memory) reports FEDBM_ETIMEOUT            */
 } fedbm_params;
 
 typedef struct fedbm_info_t {
@@ -203,19 +225,25 @@ int fedbm_rk_step(fedbm_solver* s, int32_t nsteps);
 int fedbm_rk_stage(fedbm_solver* s, int32_t stage);
 
 /* Node moments rho, u_x, u_y [K][Np] in FP64 of the current state.
- * Synchronous for host outputs. */
+ * Synchronous for host outputs; with host outputs it also returns ETIMEOUT if
+ * a stage kernel since the last state load gave up a bounded wait (the state
+ * is then only partly updated).  That timeout word stays set until the next
+ * fedbm_set_state / fedbm_set_equilibrium; fedbm_rk_step is asynchronous and
+ * cannot report it itself. */
 int fedbm_get_moments(fedbm_solver* s, double* rho, double* ux, double* uy, int32_t on_device);
 
 /* Decode the current state into canonical FP64 f[K][Np][Q].  Synchronous for
- * host output. */
+ * host output, and then reports ETIMEOUT as fedbm_get_moments does. */
 int fedbm_get_state(fedbm_solver* s, double* f, int32_t on_device);
 
 /* Decode the LSRK residual register into canonical FP64 [K][Np][Q]. */
 int fedbm_get_residual(fedbm_solver* s, double* res, int32_t on_device);
 
-/* Global mass sum_k J_k 1^T M rho_k accumulated in FP64 (synchronous).
- * Returns ENONFINITE if any node has a non-finite value or rho <= 0, and
- * ETIMEOUT if a stage kernel reported a bounded wait that gave up. */
+/* Global mass sum_k J_k 1^T M rho_k (synchronous), every stored value decoded
+ * and summed in FP64 (the velocity sum of each node too, whatever the storage
+ * precision).  Returns ENONFINITE if any node has a non-finite value or
+ * rho <= 0, and ETIMEOUT if a stage kernel since the last state load reported
+ * a bounded wait that gave up. */
 int fedbm_mass(fedbm_solver* s, double* total_mass);
 
 int fedbm_info(const fedbm_solver* s, fedbm_info_t* info);
@@ -291,9 +319,14 @@ int fedbm_autotune(fedbm_solver* s, const char* cache_path, int32_t trials);
  * nodes plus a status word, 65,792 bytes) is a fixed __device__ array that
  * every GPU loading the library holds until the process exits.  Capacity:
  * K * Np <= 2,097,152 nodes; larger inputs return FEDBM_EINVAL with a message
- * and launch nothing.  The first call on each device looks up the scratch
- * address with that device current, so make it before any stream capture.
- * All calls share the one scratch array: calls that may overlap on the GPU
+ * and launch nothing.  The scratch's device address belongs to the CUDA
+ * context that is current at the call (a context loads its own copy of the
+ * array): the first call in each context (the device's primary context, a
+ * driver-API context of the caller's, or the new primary context after
+ * cudaDeviceReset) looks the address up with cudaGetSymbolAddress and caches it
+ * under the context's unique ID, so make that first call before any stream
+ * capture.  All calls in one context share the one scratch array; every call
+ * clears the status word before use, but calls that may overlap on the GPU
  * (different streams without ordering) race and give wrong results.
  * Errors: EINVAL (null pointer, sizes), ECUDA. */
 int fedbm_mass_noalloc(const double* f, const double* jac, const double* mass_colsum,

@@ -82,8 +82,12 @@ def tau_from_kn(kn, L=1.0, cs=1.0):
 
 
 class Problem:
-    """One DG discrete-velocity BGK problem on a structured split-square mesh.
+    """One DG discrete-velocity BGK problem on a triangle mesh of a rectangle.
 
+    The mesh is the structured Nx x Ny split-square mesh, or, when `mesh` =
+    (vert_xy [nv, 2], tri [nt, 3]) is given, that conforming triangulation of
+    [0, Lx] x [0, Ly] (counter-clockwise triangles; Nx, Ny, Lx, Ly are then
+    ignored and the rectangle is read off the vertices).
     bc: 4 side kinds ('periodic' | 'diffuse' | 'eq') for sides
         0 (y=0), 1 (x=Lx), 2 (y=Ly), 3 (x=0); wall_u: 4 wall velocities.
     """
@@ -92,7 +96,7 @@ class Problem:
                  beta=1.0, bc=("diffuse", "periodic", "diffuse", "periodic"),
                  wall_u=((-0.1, 0.0), (0.0, 0.0), (0.1, 0.0), (0.0, 0.0)),
                  cfl=0.5, dt=None, collision=True, Lx=1.0, Ly=1.0,
-                 nc_extent=4.0, nc_scale=1.0):
+                 nc_extent=4.0, nc_scale=1.0, mesh=None):
         self.Nx, self.Ny, self.p = Nx, Ny, p
         kind, n = velset
         self.ex, self.ey, self.w = _velset.velocity_set(kind, n, nc_extent, nc_scale)
@@ -107,7 +111,11 @@ class Problem:
         assert (bc[0] == "periodic") == (bc[2] == "periodic")
         self.ops = _ops.RefOps(p)
         self.Np, self.Nfp = self.ops.Np, self.ops.Nfp
-        self.vx, self.vy = _mesh.structured_mesh(Nx, Ny, Lx, Ly)
+        if mesh is None:
+            self.vx, self.vy = _mesh.structured_mesh(Nx, Ny, Lx, Ly)
+        else:
+            self.vx, self.vy = _mesh.element_vertices(*mesh)
+            Lx, Ly = float(self.vx.max()), float(self.vy.max())
         self.K = self.vx.shape[0]
         self.geo = _ops.geometry(self.vx, self.vy)
         self.x, self.y = _ops.physical_nodes(self.ops, self.vx, self.vy)

@@ -1,6 +1,6 @@
-"""Structured triangulation and face connectivity (Sec. II.B.1; Sec. III.A
-builds its grids by splitting Cartesian squares into two triangles).
-Test infrastructure only.
+"""Triangulations and face connectivity (Sec. II.B.1; Sec. III.A builds its
+grids by splitting Cartesian squares into two triangles, Sec. III.B runs the
+cavity on unstructured meshes).  Test infrastructure only.
 
 Element numbering (a definition shared, as a convention, with the CUDA
 library): square (ix, iy) of an Nx x Ny grid on [0, Lx] x [0, Ly] has corners
@@ -32,6 +32,15 @@ def structured_mesh(Nx, Ny, Lx=1.0, Ly=1.0):
                     vx[base + t, v] = tri[v][0]
                     vy[base + t, v] = tri[v][1]
     return vx, vy
+
+
+def element_vertices(vert_xy, tri):
+    """Vertex coordinates vx, vy [K, 3] of a triangulation given as vertices
+    [nv, 2] and counter-clockwise triangles [K, 3] (vertex indices); the faces
+    of element k then join its vertices f and (f+1) mod 3 as above."""
+    v = np.asarray(vert_xy, dtype=np.float64)
+    t = np.asarray(tri, dtype=np.int64)
+    return v[t, 0].copy(), v[t, 1].copy()
 
 
 def boundary_side(x0, y0, x1, y1, Lx, Ly, tol=1e-12):

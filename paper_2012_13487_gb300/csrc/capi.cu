@@ -268,12 +268,41 @@ __global__ void moments_kernel(const void* in, const float* scale, const typenam
   }
 }
 
-// mass partial sums: sum over nodes of J_k mw_n rho; flags non-finite / rho <= 0
+// rho of one node row summed in FP64 over its velocities: one warp per node,
+// 16-byte loads, every stored value decoded to FP64 (exact for FP32 state; for
+// the deviation forms f = w + (w s) q with w from the FP64 velocity table),
+// FP64 lane sums and an FP64 warp reduction.  The mass diagnostic resolves
+// conservation drift far below FP32 rounding of a velocity sum this way.
 template <class ST>
-__global__ void mass_partial_kernel(const void* in, const float* scale, const typename ST::R* vel, const double* Jk,
+__device__ __forceinline__ double node_rho64(const typename ST::S* row, const double* w64, int Qp, double s,
+                                             int lane) {
+  using S = typename ST::S;
+  constexpr int V = 16 / sizeof(S);  // values per 16-byte load (Qp is a multiple of 8)
+  double m0 = 0.0;
+#pragma unroll 4
+  for (int i = lane * V; i < Qp; i += 32 * V) {
+    __align__(16) S q[V];
+    *reinterpret_cast<uint4*>(q) = *reinterpret_cast<const uint4*>(row + i);
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      if constexpr (ST::dev) {
+        const double w = w64[i + j];
+        m0 += w + w * s * double(ST::to_r(q[j]));
+      } else {
+        m0 += double(q[j]);
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) m0 += __shfl_xor_sync(0xffffffffu, m0, off);
+  return m0;
+}
+
+// mass partial sums: sum over nodes of J_k mw_n rho, all in FP64; flags
+// non-finite / rho <= 0
+template <class ST>
+__global__ void mass_partial_kernel(const void* in, const float* scale, const double* w64, const double* Jk,
                                     const double* mw, int64_t K, int Np, int Qp, double* partial, int* flag) {
   using S = typename ST::S;
-  using R = typename ST::R;
   __shared__ double red[32];
   const int lane = threadIdx.x & 31;
   const int64_t nodes = K * Np;
@@ -282,10 +311,8 @@ __global__ void mass_partial_kernel(const void* in, const float* scale, const ty
   for (int64_t kn = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; kn < nodes; kn += nw) {
     const S* row = static_cast<const S*>(in) + kn * Qp;
     const int64_t k = kn / Np;
-    const R s = ST::dev ? R(scale[k]) : R(0);
-    R rho_r, m1, m2;
-    node_sums<ST>(row, vel, Qp, s, lane, rho_r, m1, m2);
-    const double rho = double(rho_r);
+    const double s = ST::dev ? double(scale[k]) : 0.0;
+    const double rho = node_rho64<ST>(row, w64, Qp, s, lane);
     if (lane == 0) {
       if (!(rho > 0.0) || !isfinite(rho)) atomicOr(flag, 1);
       acc += Jk[k] * mw[kn % Np] * rho;
@@ -318,8 +345,22 @@ __global__ void mass_final_kernel(const double* partial, int n, double* out) {
 constexpr int kMassBlocks = 1024;
 constexpr int kMassThreads = 256;
 
+// SM count of the current device (queried once per device; 152 on GB300).
+int sm_count() {
+  static std::mutex mu;
+  static int cache[256] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 152;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[dev] && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    cache[dev] = 152;
+  return cache[dev];
+}
+
+// Grid of a grid-stride elementwise kernel: enough blocks for n threads, at
+// most 32 resident blocks per SM.
 int grid_for(int64_t n, int block) {
-  return int(std::min<int64_t>((n + block - 1) / block, 152 * 32));
+  return int(std::max<int64_t>(1, std::min<int64_t>((n + block - 1) / block, int64_t(sm_count()) * 32)));
 }
 
 
@@ -720,6 +761,9 @@ int build_group(Batch& b, Group& g) {
     Case& cs = b.cases[g.cases[lc]];
     Mesh m;
     if (!build_mesh(cs.md, m, err)) return fail(FEDBM_EINVAL, err);
+    // an unstructured mesh's caller arrays are read only during creation
+    cs.md.vert_xy = nullptr;
+    cs.md.tri = nullptr;
     cs.local = lc;
     cs.k_off = g.K;
     cs.K = m.K;
@@ -883,17 +927,13 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
          for (Group& g : b->groups) {
            const int epc = g.epc, tpb = g.tpb, st = g.nstages;
            if ((r = build_group(*b, g)) != FEDBM_OK) return r;
-           // default: tensor cores for FP32 state with 128 or 256 padded
-           // velocities up to degree 4 (the autotuner times both forms; with
-           // its compile-time operator tables the FMA kernel is now the faster
-           // one there too, 2.52e11 vs 2.04e11-2.20e11 DOF-stage/s); the 16-bit forms (the FMA kernel encodes BF16
-           // in its update and keeps more CTAs per SM), the eight dependent
-           // MMA rounds of 1024 velocities, the few stacked tiles of small
-           // 16-velocity meshes and the two CTAs per SM of degree 5 make the
-           // FMA kernel the faster one elsewhere
-           const bool want_tc = g.tc_mode > 0 || (g.tc_mode == 0 && epc == 0 && tpb == 0 && st == 0 &&
-                                                   g.store == kStoreF32 && g.Qp >= 128 && g.Qp <= 256 &&
-                                                   g.p <= 4 && tc_available(g));
+           // default: the FMA kernel for every form (with its compile-time
+           // operator tables it measured faster than the tensor-core form on
+           // FP32 state too, 2.52e11 vs 2.04e11-2.20e11 DOF-stage/s at 256
+           // velocities; the 16-bit forms, 1024 velocities, stacked 16-velocity
+           // tiles and degree 5 likewise); tensor cores on request
+           // (tensor_cores = 1) or when the autotuner times them faster
+           const bool want_tc = g.tc_mode > 0;
            if (want_tc) {
              if ((r = configure_tc(*b, g)) != FEDBM_OK) return r;
            } else if ((r = configure_tiles(*b, g, epc, tpb, st)) != FEDBM_OK) {
@@ -925,6 +965,19 @@ int ensure_staging(Batch& b, size_t elems) {
   return FEDBM_OK;
 }
 
+// Queue a copy of the group's stage-kernel timeout word into *word (host);
+// read it after the stream has been synchronised.
+int queue_timeout_read(const Batch& b, const Group& g, int* word) {
+  FEDBM_CK(cudaMemcpyAsync(word, g.flag + 1, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+  return FEDBM_OK;
+}
+
+int timeout_status(int word) {
+  return word ? fail(FEDBM_ETIMEOUT, "a stage kernel's bounded wait for its tile copies gave up; the state is "
+                                     "partly updated (load a new state to clear this)")
+              : FEDBM_OK;
+}
+
 // canonical FP64 (device) -> internal state of case c
 int encode_case(Batch& b, int c, const double* src) {
   const Case& cs = b.cases[c];
@@ -939,6 +992,8 @@ int encode_case(Batch& b, int c, const double* src) {
     default: encode_kernel<StoreF16><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__half*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
   }
   FEDBM_CK(cudaGetLastError());
+  // a new state starts with a clear stage-kernel timeout word
+  FEDBM_CK(cudaMemsetAsync(g.flag + 1, 0, sizeof(int), b.stream));
   b.time = 0;
   b.steps = 0;
   return FEDBM_OK;
@@ -1004,8 +1059,12 @@ int get_state(Batch& b, int c, double* f, int on_device) {
   }
   FEDBM_CK(cudaGetLastError());
   if (!on_device) {
+    int word = 0;
     FEDBM_CK(cudaMemcpyAsync(f, dst, n * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+    int rc = queue_timeout_read(b, g, &word);
+    if (rc) return rc;
     FEDBM_CK(cudaStreamSynchronize(b.stream));
+    return timeout_status(word);
   }
   return FEDBM_OK;
 }
@@ -1077,7 +1136,11 @@ int get_moments(Batch& b, int c, double* rho, double* ux, double* uy, int on_dev
     if (rho) FEDBM_CK(cudaMemcpyAsync(rho, dr, bytes, cudaMemcpyDeviceToHost, b.stream));
     if (ux) FEDBM_CK(cudaMemcpyAsync(ux, dx, bytes, cudaMemcpyDeviceToHost, b.stream));
     if (uy) FEDBM_CK(cudaMemcpyAsync(uy, dy, bytes, cudaMemcpyDeviceToHost, b.stream));
+    int word = 0;
+    int rc = queue_timeout_read(b, g, &word);
+    if (rc) return rc;
     FEDBM_CK(cudaStreamSynchronize(b.stream));
+    return timeout_status(word);
   }
   return FEDBM_OK;
 }
@@ -1087,9 +1150,8 @@ void launch_mass(const Group& g, int cur, const Case& cs, int blocks, cudaStream
   using S = typename ST::S;
   const S* in = static_cast<const S*>(g.f[cur]) + size_t(cs.k_off) * g.Np * g.Qp;
   const float* sc = g.scale[cur] ? g.scale[cur] + cs.k_off : nullptr;
-  using R = typename ST::R;
-  mass_partial_kernel<ST><<<blocks, kMassThreads, 0, st>>>(in, sc, static_cast<const R*>(g.vel), g.Jk + cs.k_off,
-                                                           g.mw, cs.K, g.Np, g.Qp, g.partial, g.flag);
+  mass_partial_kernel<ST><<<blocks, kMassThreads, 0, st>>>(in, sc, g.vel64 + 2 * g.Qp, g.Jk + cs.k_off, g.mw, cs.K,
+                                                           g.Np, g.Qp, g.partial, g.flag);
 }
 
 int mass(Batch& b, int c, double* total) {
@@ -1113,7 +1175,7 @@ int mass(Batch& b, int c, double* total) {
   FEDBM_CK(cudaMemcpyAsync(total, g.partial + kMassBlocks, sizeof(double), cudaMemcpyDeviceToHost, b.stream));
   FEDBM_CK(cudaMemcpyAsync(flag, g.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, b.stream));
   FEDBM_CK(cudaStreamSynchronize(b.stream));
-  if (flag[1]) return fail(FEDBM_ETIMEOUT, "a stage kernel's bounded wait for its tile copies gave up");
+  if (flag[1]) return timeout_status(flag[1]);
   if (flag[0]) return fail(FEDBM_ENONFINITE, "state has a non-finite value or a node with rho <= 0");
   return FEDBM_OK;
 }

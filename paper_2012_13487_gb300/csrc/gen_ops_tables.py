@@ -1,16 +1,17 @@
-"""Writes ops_tables.inc: the FP32 Dr, Ds and LIFT operators of degrees 0..4
+"""Writes ops_tables.inc: the FP32 Dr, Ds and LIFT operators of degrees 0..5
 as compile-time tables for the FMA stage kernel.
 
 The nodal Lagrange basis of Sec. II.B.1 lives on one reference triangle, so
 Dr, Ds and LIFT depend only on the degree (and on the node set, which the paper
 leaves open: warp & blend nodes with alpha = 0 here).  The FP32 kernels can
 therefore take them as instruction immediates instead of loading them from
-constant memory.  The
-values are the library's own operators (``fedbm_ref_operators``) rounded to
-FP32 exactly as the runtime upload rounds them; a CPU test checks that the
-committed file still matches.  Degrees 5 and 6 (441 and 784 entries per
-derivative matrix) keep constant memory: folding their tables into the
-unrolled node loops makes those translation units take minutes to compile.  Run as
+constant memory.  The values are the library's own operators
+(``fedbm_ref_operators``) rounded to FP32 exactly as the runtime upload rounds
+them; a CPU test checks that the committed file still matches.  Degree 6 (784
+entries per derivative matrix) keeps constant memory, and at degree 5 only the
+kernels that the workloads use take the table (the kernel selects them), since
+folding the tables into every unrolled node loop makes those translation units
+take many minutes to compile.  Run as
 ``python -m paper_2012_13487_gb300.csrc.gen_ops_tables`` after a build.
 """
 import os
@@ -19,7 +20,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "ops_tables.inc")
-MAX_P = 4
+MAX_P = 5
 
 
 def table(p):

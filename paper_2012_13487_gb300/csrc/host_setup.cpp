@@ -13,7 +13,9 @@
 // mass matrices.
 //
 // Mesh (Sec. III): Cartesian cells split along the lower-left/upper-right
-// diagonal; neighbours and face orientation follow from the cell structure.
+// diagonal, where neighbours and face orientation follow from the cell
+// structure, or a general conforming triangulation of a rectangle given by its
+// vertices and triangles, where neighbours are matched by shared edges.
 #include "host_setup.h"
 
 #include <algorithm>
@@ -463,11 +465,43 @@ bool build_ref_ops(int p, RefOps& o, std::string& err) {
   return true;
 }
 
-bool build_mesh(const fedbm_mesh_desc& d, Mesh& m, std::string& err) {
-  if (d.nx < 1 || d.ny < 1 || int64_t(d.nx) * d.ny > (int64_t(1) << 26)) {
-    err = "mesh: nx, ny must be >= 1 and 2*nx*ny < 2^27";
-    return false;
+namespace {
+
+// Affine geometric factors, outward unit normals and Fscale = |face| / (2 J)
+// of element k from its counter-clockwise vertices (Sec. II.B.1; J is the
+// Jacobian of the map from the reference triangle of area 2).
+void element_geometry(Mesh& m, int64_t k, double& rin_min) {
+  const double* X = &m.vx[k * 3];
+  const double* Y = &m.vy[k * 3];
+  const double xr = 0.5 * (X[1] - X[0]), xs = 0.5 * (X[2] - X[0]);
+  const double yr = 0.5 * (Y[1] - Y[0]), ys = 0.5 * (Y[2] - Y[0]);
+  const double J = xr * ys - xs * yr;
+  double* g = &m.geo[k * kGeoStride];
+  g[0] = ys / J;   // rx
+  g[1] = -yr / J;  // sx
+  g[2] = -xs / J;  // ry
+  g[3] = xr / J;   // sy
+  double perim = 0.0;
+  for (int f = 0; f < 3; ++f) {
+    const int a = f, b = (f + 1) % 3;
+    const double dx = X[b] - X[a], dy = Y[b] - Y[a];
+    const double len = std::sqrt(dx * dx + dy * dy);
+    perim += len;
+    g[4 + 3 * f + 0] = dy / len;
+    g[4 + 3 * f + 1] = -dx / len;
+    g[4 + 3 * f + 2] = 0.5 * len / J;
   }
+  g[13] = J;
+  rin_min = std::min(rin_min, 2.0 * (2.0 * J) / perim);  // area = 2J
+}
+
+// Face node order runs with the counter-clockwise direction on faces 0 and 1
+// and against it on face 2; two counter-clockwise elements sharing an edge
+// traverse it in opposite directions, so their face nodes are listed in
+// opposite order exactly when both or neither of the two faces is face 2.
+int face_rev(int f, int g) { return int((f == 2) == (g == 2)); }
+
+bool check_sides(const fedbm_mesh_desc& d, std::string& err) {
   for (int sd = 0; sd < 4; ++sd) {
     if (d.bc[sd] < FEDBM_BC_PERIODIC || d.bc[sd] > FEDBM_BC_WALL_EQ) {
       err = "mesh: unknown boundary kind";
@@ -487,6 +521,159 @@ bool build_mesh(const fedbm_mesh_desc& d, Mesh& m, std::string& err) {
       return false;
     }
   }
+  return true;
+}
+
+// General conforming triangulation of the rectangle [0, lx] x [0, ly]
+// (Sec. III.B runs the cavity on unstructured meshes).  Neighbours are found
+// by matching the vertex pairs of the element edges; boundary edges are given
+// the side of the rectangle they lie on, and periodic sides are paired by the
+// coordinates of their end points.
+bool build_unstructured(const fedbm_mesh_desc& d, Mesh& m, std::string& err) {
+  if (!d.vert_xy || !d.tri || d.nvert < 3 || d.ntri < 1 || d.ntri > (int64_t(1) << 27)) {
+    err = "mesh: an unstructured mesh needs nvert >= 3, 1 <= ntri < 2^27 and both arrays";
+    return false;
+  }
+  const int64_t K = d.ntri;
+  double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+  for (int v = 0; v < d.nvert; ++v) {
+    const double x = d.vert_xy[2 * v], y = d.vert_xy[2 * v + 1];
+    if (!std::isfinite(x) || !std::isfinite(y)) {
+      err = "mesh: vertex coordinates must be finite";
+      return false;
+    }
+    xmin = std::min(xmin, x);
+    xmax = std::max(xmax, x);
+    ymin = std::min(ymin, y);
+    ymax = std::max(ymax, y);
+  }
+  const double ext = std::max(xmax - xmin, ymax - ymin);
+  const double tol = 1e-10 * ext;
+  if (!(ext > 0) || std::fabs(xmin) > tol || std::fabs(ymin) > tol) {
+    err = "mesh: the vertices must span a rectangle [0, lx] x [0, ly]";
+    return false;
+  }
+  m.nx = m.ny = 0;
+  m.K = K;
+  m.lx = xmax;
+  m.ly = ymax;
+  m.vx.assign(size_t(K) * 3, 0.0);
+  m.vy.assign(size_t(K) * 3, 0.0);
+  m.nbr.assign(size_t(K) * 3, 0);
+  m.geo.assign(size_t(K) * kGeoStride, 0.0);
+  double rin_min = 1e300;
+  struct Edge {
+    int64_t lo, hi, k;
+    int f;
+  };
+  std::vector<Edge> edges;
+  edges.reserve(size_t(K) * 3);
+  for (int64_t k = 0; k < K; ++k) {
+    int32_t v[3];
+    for (int j = 0; j < 3; ++j) {
+      v[j] = d.tri[k * 3 + j];
+      if (v[j] < 0 || v[j] >= d.nvert) {
+        err = "mesh: triangle " + std::to_string(k) + " has a vertex index out of range";
+        return false;
+      }
+      m.vx[k * 3 + j] = d.vert_xy[2 * v[j]];
+      m.vy[k * 3 + j] = d.vert_xy[2 * v[j] + 1];
+    }
+    const double* X = &m.vx[k * 3];
+    const double* Y = &m.vy[k * 3];
+    const double area2 = (X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]);
+    if (!(area2 > 1e-14 * ext * ext)) {
+      err = "mesh: triangle " + std::to_string(k) + " is degenerate or not counter-clockwise";
+      return false;
+    }
+    element_geometry(m, k, rin_min);
+    for (int f = 0; f < 3; ++f) {
+      const int64_t a = v[f], b = v[(f + 1) % 3];
+      edges.push_back({std::min(a, b), std::max(a, b), k, f});
+    }
+  }
+  std::sort(edges.begin(), edges.end(), [](const Edge& x, const Edge& y) {
+    return x.lo != y.lo ? x.lo < y.lo : (x.hi != y.hi ? x.hi < y.hi : (x.k != y.k ? x.k < y.k : x.f < y.f));
+  });
+  // boundary edges per side, keyed by the coordinate along the side of their
+  // end points (sorted) for periodic pairing
+  struct Bnd {
+    double t0, t1;
+    int64_t k;
+    int f;
+  };
+  std::vector<Bnd> bnd[4];
+  for (size_t e = 0; e < edges.size();) {
+    size_t n = 1;
+    while (e + n < edges.size() && edges[e + n].lo == edges[e].lo && edges[e + n].hi == edges[e].hi) ++n;
+    if (n > 2) {
+      err = "mesh: an edge is shared by more than two triangles";
+      return false;
+    }
+    if (n == 2) {
+      const Edge& A = edges[e];
+      const Edge& B = edges[e + 1];
+      if (d.tri[A.k * 3 + A.f] == d.tri[B.k * 3 + B.f]) {
+        err = "mesh: two triangles traverse a shared edge in the same direction";
+        return false;
+      }
+      m.nbr[A.k * 3 + A.f] = encode_face(B.k, B.f, face_rev(A.f, B.f));
+      m.nbr[B.k * 3 + B.f] = encode_face(A.k, A.f, face_rev(B.f, A.f));
+    } else {
+      const Edge& A = edges[e];
+      const double x0 = d.vert_xy[2 * A.lo], y0 = d.vert_xy[2 * A.lo + 1];
+      const double x1 = d.vert_xy[2 * A.hi], y1 = d.vert_xy[2 * A.hi + 1];
+      int side = -1;
+      if (std::fabs(y0) <= tol && std::fabs(y1) <= tol) side = 0;
+      else if (std::fabs(x0 - xmax) <= tol && std::fabs(x1 - xmax) <= tol) side = 1;
+      else if (std::fabs(y0 - ymax) <= tol && std::fabs(y1 - ymax) <= tol) side = 2;
+      else if (std::fabs(x0) <= tol && std::fabs(x1) <= tol) side = 3;
+      if (side < 0) {
+        err = "mesh: a boundary edge of triangle " + std::to_string(A.k) + " is not on a side of the rectangle";
+        return false;
+      }
+      const double t0 = (side == 0 || side == 2) ? std::min(x0, x1) : std::min(y0, y1);
+      const double t1 = (side == 0 || side == 2) ? std::max(x0, x1) : std::max(y0, y1);
+      bnd[side].push_back({t0, t1, A.k, A.f});
+      m.nbr[A.k * 3 + A.f] = -(side + 1);
+    }
+    e += n;
+  }
+  for (int sd = 0; sd < 2; ++sd) {  // pairs (0, 2) and (1, 3)
+    const int op = sd + 2;
+    if (d.bc[sd] != FEDBM_BC_PERIODIC) continue;
+    auto by_t = [](const Bnd& x, const Bnd& y) { return x.t0 < y.t0; };
+    std::sort(bnd[sd].begin(), bnd[sd].end(), by_t);
+    std::sort(bnd[op].begin(), bnd[op].end(), by_t);
+    if (bnd[sd].size() != bnd[op].size()) {
+      err = "mesh: periodic sides do not have matching edges";
+      return false;
+    }
+    for (size_t j = 0; j < bnd[sd].size(); ++j) {
+      const Bnd& A = bnd[sd][j];
+      const Bnd& B = bnd[op][j];
+      if (std::fabs(A.t0 - B.t0) > tol || std::fabs(A.t1 - B.t1) > tol) {
+        err = "mesh: periodic sides do not have matching edges";
+        return false;
+      }
+      m.nbr[A.k * 3 + A.f] = encode_face(B.k, B.f, face_rev(A.f, B.f));
+      m.nbr[B.k * 3 + B.f] = encode_face(A.k, A.f, face_rev(B.f, A.f));
+    }
+  }
+  m.rin_min = rin_min;
+  return true;
+}
+
+}  // namespace
+
+bool build_mesh(const fedbm_mesh_desc& d, Mesh& m, std::string& err) {
+  if (!check_sides(d, err)) return false;
+  if (d.ntri > 0 || d.nvert > 0 || d.tri || d.vert_xy) return build_unstructured(d, m, err);
+  if (d.nx < 1 || d.ny < 1 || int64_t(d.nx) * d.ny > (int64_t(1) << 26)) {
+    err = "mesh: nx, ny must be >= 1 and 2*nx*ny < 2^27";
+    return false;
+  }
+  const bool perx = d.bc[1] == FEDBM_BC_PERIODIC, pery = d.bc[0] == FEDBM_BC_PERIODIC;
   m.nx = d.nx;
   m.ny = d.ny;
   m.lx = d.lx > 0 ? d.lx : 1.0;
@@ -498,11 +685,7 @@ bool build_mesh(const fedbm_mesh_desc& d, Mesh& m, std::string& err) {
   m.nbr.assign(size_t(m.K) * 3, 0);
   m.geo.assign(size_t(m.K) * kGeoStride, 0.0);
   const double hx = m.lx / nx, hy = m.ly / ny;
-  // face node order runs with the counter-clockwise direction on faces 0, 1 and
-  // against it on face 2; two faces sharing an edge traverse it in opposite
-  // counter-clockwise directions, so their node orders are reversed exactly
-  // when both or neither of them is face 2.
-  auto rev = [](int f, int g) { return int((f == 2) == (g == 2)); };
+  auto rev = face_rev;
   auto elem = [nx](int ix, int iy, int t) { return int64_t(2) * (int64_t(iy) * nx + ix) + t; };
   double rin_min = 1e300;
   for (int iy = 0; iy < ny; ++iy) {
@@ -534,29 +717,7 @@ bool build_mesh(const fedbm_mesh_desc& d, Mesh& m, std::string& err) {
           if (ix > 0) nb[2] = encode_face(elem(ix - 1, iy, 0), 1, rev(2, 1));
           else nb[2] = perx ? encode_face(elem(nx - 1, iy, 0), 1, rev(2, 1)) : -(3 + 1);
         }
-        // affine geometric factors
-        const double* X = &m.vx[k * 3];
-        const double* Y = &m.vy[k * 3];
-        const double xr = 0.5 * (X[1] - X[0]), xs = 0.5 * (X[2] - X[0]);
-        const double yr = 0.5 * (Y[1] - Y[0]), ys = 0.5 * (Y[2] - Y[0]);
-        const double J = xr * ys - xs * yr;
-        double* g = &m.geo[k * kGeoStride];
-        g[0] = ys / J;   // rx
-        g[1] = -yr / J;  // sx
-        g[2] = -xs / J;  // ry
-        g[3] = xr / J;   // sy
-        double perim = 0.0;
-        for (int f = 0; f < 3; ++f) {
-          const int a = f, b = (f + 1) % 3;
-          const double dx = X[b] - X[a], dy = Y[b] - Y[a];
-          const double len = std::sqrt(dx * dx + dy * dy);
-          perim += len;
-          g[4 + 3 * f + 0] = dy / len;
-          g[4 + 3 * f + 1] = -dx / len;
-          g[4 + 3 * f + 2] = 0.5 * len / J;
-        }
-        g[13] = J;
-        rin_min = std::min(rin_min, 2.0 * (2.0 * J) / perim);  // area = 2J
+        element_geometry(m, k, rin_min);
       }
     }
   }

@@ -9,6 +9,7 @@
 // Its scratch lives in one file-scope __device__ array of fixed size that the
 // CUDA runtime places in every device's memory when the library is loaded and
 // that stays there until the process exits.
+#include <cuda.h>  // driver API types only; the functions come from cudaGetDriverEntryPointByVersion
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,33 +35,83 @@ constexpr size_t kScratchBytes = size_t(kMaxBlocks) * sizeof(double) + 256;  // 
 // from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_mass_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_mutex;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
+// The symbol's device address belongs to a CUDA context (the module is loaded
+// once per context), not to a device ordinal: cudaDeviceReset or a driver-API
+// context of its own gives the same device another copy of the array.  The
+// address is therefore cached per context, keyed by the context's unique ID
+// (cuCtxGetId; a context created after a reset gets a new ID even if its
+// handle value repeats).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
 
-// Device address of the scratch on the current device (looked up once per device).
-int scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    fedbm::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    return FEDBM_ECUDA;
-  }
-  if (dev < 0 || dev >= kMaxDevices) {
-    fedbm::set_last_error("device ordinal out of range");
-    return FEDBM_EINVAL;
-  }
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_mass_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      fedbm::set_last_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+constexpr int kCacheSlots = 64;
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;
+  unsigned char* addr = nullptr;
+};
+std::mutex g_mutex;
+ScratchSlot g_cache[kCacheSlots];
+int g_next_slot = 0;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+int cuda_fail(const char* what, cudaError_t e) {
+  fedbm::set_last_error(std::string("fedbm_mass_noalloc: ") + what + ": " + cudaGetErrorString(e));
+  return FEDBM_ECUDA;
+}
+
+// Unique ID of the calling thread's current context (0 if none is current).
+int current_context_id(unsigned long long* id) {
+  *id = 0;
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return cuda_fail("driver entry points", e);
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      fedbm::set_last_error("fedbm_mass_noalloc: the driver has no cuCtxGetCurrent/cuCtxGetId");
       return FEDBM_ECUDA;
     }
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
   }
-  *out = g_scratch_addr[dev];
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) {
+    fedbm::set_last_error("fedbm_mass_noalloc: cuCtxGetCurrent failed");
+    return FEDBM_ECUDA;
+  }
+  if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS) {
+    fedbm::set_last_error("fedbm_mass_noalloc: cuCtxGetId failed");
+    return FEDBM_ECUDA;
+  }
+  return FEDBM_OK;
+}
+
+// Device address of the scratch in the current context, looked up with
+// cudaGetSymbolAddress the first time a context calls and cached for it.
+int scratch_address(unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  unsigned long long id = 0;
+  int rc = current_context_id(&id);
+  if (rc != FEDBM_OK) return rc;
+  if (id != 0) {
+    for (const ScratchSlot& sl : g_cache)
+      if (sl.ctx_id == id && sl.addr) {
+        *out = sl.addr;
+        return FEDBM_OK;
+      }
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_mass_scratch);  // makes the device's primary context current if none is
+  if (e != cudaSuccess || p == nullptr) return cuda_fail("cudaGetSymbolAddress(scratch)", e);
+  if (id == 0 && (rc = current_context_id(&id)) != FEDBM_OK) return rc;
+  ScratchSlot& sl = g_cache[g_next_slot];
+  g_next_slot = (g_next_slot + 1) % kCacheSlots;
+  sl.ctx_id = id;
+  sl.addr = static_cast<unsigned char*>(p);
+  *out = sl.addr;
   return FEDBM_OK;
 }
 

@@ -66,25 +66,42 @@ static __constant__ unsigned long long c_ops32x2[OPS_N];
 
 #include "ops_tables.inc"
 
-template <typename R>
+// Dr, Ds, LIFT entry idx in the compute precision.  kImm: the FP32 operators
+// of this degree as a compile-time table (the operators depend only on the
+// degree, and with the node loops unrolled every entry becomes an instruction
+// immediate instead of a constant-memory load; the table holds the runtime
+// upload's values, which a CPU test checks); otherwise constant memory.
+template <typename R, bool kImm>
 __device__ __forceinline__ R opv(int idx);
-#ifdef FEDBM_OPS32_TABLE
-// FP32 operators of this degree (<= 4) as a compile-time table: the operators
-// depend only on the degree, and with the node loops unrolled every Dr, Ds and
-// LIFT entry becomes an instruction immediate instead of a constant-memory
-// load.  The table holds the runtime upload's values (a CPU test checks it).
 template <>
-__device__ __forceinline__ float opv<float>(int idx) {
+__device__ __forceinline__ float opv<float, false>(int idx) { return c_ops32[idx]; }
+template <>
+__device__ __forceinline__ double opv<double, false>(int idx) { return c_ops64[idx]; }
+#ifdef FEDBM_OPS32_TABLE
+constexpr bool kHaveOpsTable = true;
+template <>
+__device__ __forceinline__ float opv<float, true>(int idx) {
   constexpr float t[] = {FEDBM_OPS32_TABLE};
   static_assert(sizeof(t) / sizeof(t[0]) == OPS_N, "operator table of another degree");
   return t[idx];
 }
 #else
+constexpr bool kHaveOpsTable = false;
 template <>
-__device__ __forceinline__ float opv<float>(int idx) { return c_ops32[idx]; }
+__device__ __forceinline__ float opv<float, true>(int idx) { return c_ops32[idx]; }
 #endif
 template <>
-__device__ __forceinline__ double opv<double>(int idx) { return c_ops64[idx]; }
+__device__ __forceinline__ double opv<double, true>(int idx) { return c_ops64[idx]; }
+
+// Which FMA kernels take the operators as immediates: every FP32-arithmetic
+// kernel up to degree 4; at degree 5 (1,260 operator entries) only the
+// compile-time velocity counts of the FP32 and BF16 states, which keeps that
+// translation unit's compile time within a few minutes.
+template <class ST, int QT>
+__host__ __device__ constexpr bool ops_immediate() {
+  return kHaveOpsTable && sizeof(typename ST::R) == 4 &&
+         (P <= 4 || (QT > 0 && (ST::kind == kStoreF32 || ST::kind == kStoreBF16)));
+}
 
 // Node index of face node a on face f (rows of the reference triangle start at
 // a(P+1) - a(a-1)/2; face 0 is row 0, face 1 the row ends, face 2 the row starts).
@@ -189,11 +206,25 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for phase `parity` of the barrier for at most `limit_ns`; false on timeout.
+// try_wait with a suspend-time hint: a thread whose phase is not complete is
+// suspended until the phase completes or about hint_ns pass, instead of
+// returning at once, so that waiting warps do not take issue slots from the
+// warps that compute.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the barrier for at most about `limit_ns` (each
+// suspended try_wait lasts at most 20 us past the limit); false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
-  while (!mbar_try_wait(bar, parity)) {
+  while (!mbar_try_wait_suspend(bar, parity, 20000u)) {
     if (global_timer_ns() - t0 > limit_ns) return false;
   }
   return true;
@@ -432,6 +463,7 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
   const R rkA = a.rkA, rkB = a.rkB, ab = a.ab;
   const bool third = a.eq_order == 3;
   constexpr bool kPacked = FEDBM_PACKED_FMA && sizeof(R) == 4 && VPT == 2;
+  constexpr bool kImm = ops_immediate<ST, QT>();
   constexpr bool kKeep = keeps_scale<ST>();
   constexpr bool kTrack = ST::dev && !kKeep;
   for (int item = tid; item < ne * Qv; item += nth) {
@@ -531,7 +563,7 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
         for (int v = 0; v < VPT; ++v) dr[v] = ds[v] = lf[v] = R(0);
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
-          const R cr = opv<R>(OFF_DR + n * NP + m), cs = opv<R>(OFF_DS + n * NP + m);
+          const R cr = opv<R, kImm>(OFF_DR + n * NP + m), cs = opv<R, kImm>(OFF_DS + n * NP + m);
 #pragma unroll
           for (int v = 0; v < VPT; ++v) {
             dr[v] = fma(cr, fr[v][m], dr[v]);
@@ -540,7 +572,7 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
         }
 #pragma unroll
         for (int j = 0; j < NF; ++j) {
-          const R cl = opv<R>(OFF_LIFT + n * NF + j);
+          const R cl = opv<R, kImm>(OFF_LIFT + n * NF + j);
 #pragma unroll
           for (int v = 0; v < VPT; ++v) lf[v] = fma(cl, flux[v][j], lf[v]);
         }
@@ -703,13 +735,21 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
         issue_tile_loads<ST, QT>(a, sm, k0, ne, read_res);
       }
     }
-    if (!mbar_wait_bounded(sm.bar, parity, 2000000000ull)) {
-      if (a.err) atomicExch(a.err, 1);
+    // warp 0 waits for the tile (suspended in try_wait); the other warps
+    // wait at the block barrier, where they take no issue slots
+    bool ok = true;
+    if (tid < 32) ok = mbar_wait_bounded(sm.bar, parity, 2000000000ull);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && a.err) atomicExch(a.err, 1);
       // let copies still in flight land before the CTA exits
-      if (two && next < ntiles) mbar_wait_bounded(stage((j + 1) & 1).bar, uint32_t(((j + 1) >> 1) & 1), 1000000000ull);
+      if (tid < 32 && two && next < ntiles)
+        mbar_wait_bounded(stage((j + 1) & 1).bar, uint32_t(((j + 1) >> 1) & 1), 1000000000ull);
       if (tid == 0) bulk_wait_read();
       return;
     }
+    // the phase is complete: one try_wait gives every other thread its own
+    // acquire of the copied data
+    if (tid >= 32) mbar_try_wait(sm.bar, parity);
 
     // ---- 2. node moments ---------------------------------------------------------
     if (!a.collision) {

@@ -303,16 +303,21 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
 
   bool failed = false;
   int pending = -1;   // parity of a tile copy issued but not yet waited for
+  int mma_pending = -1;  // phase of committed MMAs whose barrier wait gave up
   uint32_t mph = 0;   // phase of the MMA barrier
   for (int j = 0; tile < ntiles; ++j, tile += gridDim.x) {
     const int ne = tile_ne(tile);
     const bool valid = te < ne;                  // a ragged tail leaves rows empty
     const int64_t k0 = tile * EPT + te;          // this row's element
-    const bool ok = mbar_wait_bounded(bar_tile, uint32_t(j & 1), 2000000000ull);
+    // warp 0 waits for the tile (suspended in try_wait), the others at the
+    // block barrier; then one try_wait gives each thread its acquire
+    bool ok = true;
+    if (tid < 32) ok = mbar_wait_bounded(bar_tile, uint32_t(j & 1), 2000000000ull);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
     }
+    if (tid >= 32) mbar_try_wait(bar_tile, uint32_t(j & 1));
     pending = -1;
 
     // ---- node moments and wall numerators (as in the FMA kernel) -----------------
@@ -415,12 +420,15 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
       if (!last) fetch(k0, i + kTcThreads, rnext, tnext, snext);
       else if (tile + gridDim.x < ntiles) fetch(row_elem(tile + gridDim.x), ti, rnext, tnext, snext);
 
-      const bool mok = mbar_wait_bounded(bar_mma, mph, 2000000000ull);
-      mph ^= 1u;
+      bool mok = true;
+      if (tid < 32) mok = mbar_wait_bounded(bar_mma, mph, 2000000000ull);
       if (__syncthreads_or(!mok)) {
         failed = true;
+        mma_pending = int(mph);  // the MMAs may still write tensor memory
         break;
       }
+      if (tid >= 32) mbar_try_wait(bar_mma, mph);
+      mph ^= 1u;
       fence_after_sync();
 
       // ---- epilogue: rhs, collision, update; outputs straight from registers -------
@@ -504,6 +512,8 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
     if (tid == 0 && a.err) atomicExch(a.err, 1);
     // a copy of the next tile may still be in flight: let it land (bounded)
     if (pending >= 0) mbar_wait_bounded(bar_tile, uint32_t(pending), 1000000000ull);
+    // committed MMAs must finish with tensor memory before it is released (bounded)
+    if (mma_pending >= 0) mbar_wait_bounded(bar_mma, uint32_t(mma_pending), 1000000000ull);
   }
   fence_before_sync();
   __syncthreads();

@@ -30,7 +30,9 @@ RED_DEFAULT, RED_FP64, RED_COMP_FP32 = 0, 1, 2
 class MeshDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("bc", ctypes.c_int32 * 4), ("wall_ux", ctypes.c_double * 4),
-                ("wall_uy", ctypes.c_double * 4), ("lx", ctypes.c_double), ("ly", ctypes.c_double)]
+                ("wall_uy", ctypes.c_double * 4), ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("nvert", ctypes.c_int32), ("ntri", ctypes.c_int32),
+                ("vert_xy", ctypes.c_void_p), ("tri", ctypes.c_void_p)]
 
 
 class VelsetDesc(ctypes.Structure):
@@ -161,6 +163,22 @@ def mesh_desc(nx, ny, order, bc=(BC_WALL_DIFFUSE, BC_PERIODIC, BC_WALL_DIFFUSE, 
     return d
 
 
+def unstructured_mesh_desc(vert_xy, tri, order, bc=(BC_WALL_DIFFUSE,) * 4,
+                           wall_u=((0, 0), (0, 0), (0, 0), (0, 0))):
+    """Descriptor of a conforming triangulation (vertices [nv][2], counter-
+    clockwise triangles [nt][3]).  The arrays are kept alive on the returned
+    descriptor (attribute ``_keep``) because the C side reads them when the
+    descriptor is used."""
+    v = np.ascontiguousarray(vert_xy, dtype=np.float64)
+    t = np.ascontiguousarray(tri, dtype=np.int32)
+    assert v.ndim == 2 and v.shape[1] == 2 and t.ndim == 2 and t.shape[1] == 3
+    d = mesh_desc(0, 0, order, bc=bc, wall_u=wall_u, lx=0.0, ly=0.0)
+    d.nvert, d.ntri = v.shape[0], t.shape[0]
+    d.vert_xy, d.tri = v.ctypes.data, t.ctypes.data
+    d._keep = (v, t)
+    return d
+
+
 def velset_desc(kind=VELSET_GH, n=4, eq_order=2, nc_extent=4.0, nc_sqrt2=0):
     d = VelsetDesc()
     d.kind, d.n, d.eq_order, d.nc_extent, d.nc_sqrt2 = kind, n, eq_order, nc_extent, nc_sqrt2
@@ -197,8 +215,13 @@ def fedbm_ref_operators(p):
     return out
 
 
+def mesh_elements(mesh):
+    """Element count K of a mesh descriptor."""
+    return mesh.ntri if mesh.ntri > 0 else 2 * mesh.nx * mesh.ny
+
+
 def fedbm_mesh_nodes(mesh, vs=None, prm=None):
-    K = 2 * mesh.nx * mesh.ny
+    K = mesh_elements(mesh)
     Np = (mesh.order + 1) * (mesh.order + 2) // 2
     x, y = np.zeros((K, Np)), np.zeros((K, Np))
     dt = ctypes.c_double(0.0)
@@ -209,7 +232,7 @@ def fedbm_mesh_nodes(mesh, vs=None, prm=None):
 
 
 def fedbm_mesh_connectivity(mesh):
-    nbr = np.zeros((2 * mesh.nx * mesh.ny, 3), np.int32)
+    nbr = np.zeros((mesh_elements(mesh), 3), np.int32)
     _check(lib().fedbm_mesh_connectivity(ctypes.byref(mesh), _ptr(nbr)))
     return nbr
 
@@ -333,6 +356,7 @@ def fedbm_autotune(h, cache_path=None, trials=0):
 def case_desc(mesh, vs, prm):
     c = CaseDesc()
     c.mesh, c.velset, c.params = mesh, vs, prm
+    c._keep = getattr(mesh, "_keep", None)   # an unstructured mesh's arrays
     return c
 
 

@@ -63,3 +63,56 @@ def batch_cases(seed=201213487, n=256):
             vel=("gh", 4) if u[c, 4] < 0.5 else ("nc", 16),
         ))
     return out
+
+
+def unstructured_square(nx, ny, seed, jitter=0.2, shuffle=True, lx=1.0, ly=1.0):
+    """A seeded conforming triangulation of [0, lx] x [0, ly] with irregular
+    connectivity: an (nx+1) x (ny+1) vertex grid whose interior vertices are
+    moved by up to `jitter` cell widths in each direction (boundary vertices
+    slide along their side, corners stay), every cell split along a randomly
+    chosen diagonal, each triangle's vertex list rotated by a random amount
+    (it stays counter-clockwise) and, with `shuffle`, the triangles put in a
+    random order.  Opposite sides keep the same vertex positions along the
+    side, so they can be paired periodically.  Returns (vert_xy [nv, 2],
+    tri [nt, 3] int32), nt = 2 nx ny.  Draws only; no arithmetic of the method."""
+    nv = (nx + 1) * (ny + 1)
+    u = uniform01(seed, 2 * nv + 2 * nx * ny + 2 * nx * ny).reshape(-1)
+    jx = (2.0 * u[:nv] - 1.0) * jitter
+    jy = (2.0 * u[nv:2 * nv] - 1.0) * jitter
+    hx, hy = lx / nx, ly / ny
+    vert = np.zeros((nv, 2))
+    for iy in range(ny + 1):
+        for ix in range(nx + 1):
+            v = iy * (nx + 1) + ix
+            x, y = ix * hx, iy * hy
+            inner_x = 0 < ix < nx
+            inner_y = 0 < iy < ny
+            # side vertices move along their side only; a top (right) side
+            # vertex takes the draw of the bottom (left) one below (beside) it,
+            # so that opposite sides stay paired
+            if inner_x:
+                x += jx[v if inner_y else ix] * hx
+            if inner_y:
+                y += jy[v if inner_x else iy * (nx + 1)] * hy
+            vert[v] = (x, y)
+    diag = u[2 * nv:2 * nv + nx * ny] < 0.5
+    rot = (u[2 * nv + nx * ny:2 * nv + 3 * nx * ny] * 3).astype(np.int64).clip(0, 2)
+    tris = []
+    for iy in range(ny):
+        for ix in range(nx):
+            a = iy * (nx + 1) + ix
+            b, c, d = a + 1, a + nx + 2, a + nx + 1           # counter-clockwise corners
+            cell = iy * nx + ix
+            pair = ((a, b, c), (a, c, d)) if diag[cell] else ((a, b, d), (b, c, d))
+            tris.extend(pair)
+    tri = np.array(tris, dtype=np.int64)
+    r = rot[:len(tri)]
+    tri = np.stack([tri[np.arange(len(tri)), (r + j) % 3] for j in range(3)], axis=1)
+    if shuffle:
+        order = np.argsort(uniform01(seed ^ 0x5DEECE66D, len(tri)), kind="stable")
+        tri = tri[order]
+    X = vert[tri]
+    area2 = (X[:, 1, 0] - X[:, 0, 0]) * (X[:, 2, 1] - X[:, 0, 1]) - (X[:, 2, 0] - X[:, 0, 0]) * (X[:, 1, 1] - X[:, 0, 1])
+    if area2.min() < 0.1 * hx * hy:
+        raise ValueError("jitter too large: a triangle lost most of its area")
+    return vert, tri.astype(np.int32)

@@ -20,19 +20,29 @@ def cavity(nx, ny, p, U=0.1, **kw):
     return dict(nx=nx, ny=ny, p=p, bc=CAVITY_BC, wall_u=((0, 0), (0, 0), (U, 0), (0, 0)), **kw)
 
 
+def unstructured(c, nx, ny, seed=11, shuffle=True):
+    """Case c on a seeded unstructured triangulation of the unit square with
+    about as many cells (2 nx ny triangles)."""
+    return dict(c, mesh=inputs.unstructured_square(nx, ny, seed, shuffle=shuffle))
+
+
 def oracle_problem(c):
     vs = c.get("velset", ("gh", 4))
     return dg.Problem(c["nx"], c["ny"], c["p"], velset=vs, eq_order=c.get("eq_order", 2),
                       kn=c.get("kn", 1.0), beta=c.get("beta", 1.0), bc=c["bc"], wall_u=c["wall_u"],
                       cfl=c.get("cfl", 0.5), collision=c.get("collision", True),
-                      nc_scale=np.sqrt(2.0) if c.get("nc_sqrt2", False) else 1.0)
+                      nc_scale=np.sqrt(2.0) if c.get("nc_sqrt2", False) else 1.0, mesh=c.get("mesh"))
 
 
 def descriptors(c, precision="fp32", reduction="default", **tile):
     """(mesh, velset, params) descriptors of a case dict for the C ABI."""
     from paper_2012_13487_gb300 import fedbm as fb
     vs = c.get("velset", ("gh", 4))
-    m = fb.mesh_desc(c["nx"], c["ny"], c["p"], bc=tuple(BC_CODE[b] for b in c["bc"]), wall_u=c["wall_u"])
+    if c.get("mesh") is not None:
+        m = fb.unstructured_mesh_desc(c["mesh"][0], c["mesh"][1], c["p"], bc=tuple(BC_CODE[b] for b in c["bc"]),
+                                      wall_u=c["wall_u"])
+    else:
+        m = fb.mesh_desc(c["nx"], c["ny"], c["p"], bc=tuple(BC_CODE[b] for b in c["bc"]), wall_u=c["wall_u"])
     v = fb.velset_desc(fb.VELSET_GH if vs[0] == "gh" else fb.VELSET_NC, vs[1], c.get("eq_order", 2),
                        nc_sqrt2=int(c.get("nc_sqrt2", False)))
     prm = fb.params(kn=c.get("kn", 1.0), precision=PREC_CODE[precision], reduction=RED_CODE[reduction],

@@ -37,6 +37,19 @@ def test_stage_wait_timeout_reported_and_context_usable():
         s.mass()
     assert e.value.code == fb.FEDBM_ETIMEOUT
     assert time.time() - t0 < 60.0
+    # the synchronous host read-outs report it too, and it stays until a new state is loaded
+    with pytest.raises(fb.FedbmError) as e:
+        s.moments()
+    assert e.value.code == fb.FEDBM_ETIMEOUT
+    with pytest.raises(fb.FedbmError) as e:
+        s.state()
+    assert e.value.code == fb.FEDBM_ETIMEOUT
+    with pytest.raises(fb.FedbmError) as e:
+        s.mass()
+    assert e.value.code == fb.FEDBM_ETIMEOUT
+    s.set_equilibrium(1.0, 0.0, 0.0, 1e-3, 5)
+    s.mass()
+    s.moments()
     s.close()
 
     # the context still works: an ordinary solver matches the oracle

@@ -2,13 +2,19 @@
 (Kn = 8, p = 3, NC 32x32 velocities, lid speed 0.1): one LSRK(5,4) step from a
 perturbed rest state in every reduced storage form, against the FP64 oracle.
 
-Bound for the 16-bit deviation forms (f = w (1 + s q), s a power of two per
-element with |q| < 2^qmax): one encoding changes f by at most w md u, md the
-element's largest |f/w - 1| and u = 2^-8 for BF16 (8 significant bits, q in
-(-1, 1)) or 2^-11 for FP16 (11 significant bits, |q| < 2^15).  One step
-encodes six times (the initial state and the five stage outputs); the stage
-operator may amplify an input error by O(1), so the test allows 12 u.  The
-FP32 form is held to the per-stage rounding bound of the parity tests.
+Two bounds per form.  A priori, for the 16-bit deviation forms (f = w (1 + s q),
+s a power of two per element with |q| < 2^qmax): one encoding changes f by at
+most w md u, md the element's largest |f/w - 1| and u = 2^-8 for BF16 (8
+significant bits, q in (-1, 1)) or 2^-11 for FP16 (11 significant bits,
+|q| < 2^15); one step encodes six times (the initial state and the five stage
+outputs) and the stage operator may amplify an input error by O(1), so every
+value is held to 12 u.  As regression bounds, the measured errors of this
+fixed, seeded case (deterministic on the GPU) are held to about twice their
+values on the GB300 (measured: BF16 max|df|/(w md) 1.52e-2, L2 rho 1.40e-7,
+L2 u/U 1.41e-6; FP16 2.30e-3, 4.32e-8, 3.03e-7; FP32 relative max 2.32e-7,
+L2 rho 4.41e-8, L2 u/U 2.06e-7; the three moment-reduction modes agree to
+three digits, since the storage rounding dominates).  The FP32 form is also
+held to the per-stage rounding bound of the parity tests.
 """
 import numpy as np
 import pytest
@@ -52,8 +58,12 @@ def _report(pr, f, f1, rho, ux, uy):
     return float(norm_err), float(e_rho), float(e_u), e_f
 
 
-@pytest.mark.parametrize("prec,red,u", [("bf16", "fp64", 2.0 ** -8), ("bf16", "comp", 2.0 ** -8),
-                                        ("fp16", "fp64", 2.0 ** -11), ("fp16", "comp", 2.0 ** -11)])
+# regression bounds, about twice the measured errors: (max|df|/(w md), L2 rho, L2 u/U)
+MEASURED_2X = {"bf16": (3.0e-2, 3.0e-7, 3.0e-6), "fp16": (4.6e-3, 9.0e-8, 6.5e-7)}
+
+
+@pytest.mark.parametrize("prec,red,u", [(p, r, u) for p, u in (("bf16", 2.0 ** -8), ("fp16", 2.0 ** -11))
+                                        for r in ("default", "fp64", "comp")])
 def test_deviation_storage_error_c3_copy(oracle_step, prec, red, u):
     pr, f0, f1 = oracle_step
     f, rho, ux, uy = _gpu_step(f0, prec, red)
@@ -61,12 +71,16 @@ def test_deviation_storage_error_c3_copy(oracle_step, prec, red, u):
     print(f"{prec}/{red}: max|df|/(w md) = {norm_err:.3e} (bound {12 * u:.3e}), "
           f"L2 rho {e_rho:.3e}, L2 u/U {e_u:.3e}, rel L2 f {e_f:.3e}")
     assert norm_err < 12 * u, norm_err
-    assert e_rho < 12 * u and e_u < 12 * u * 10, (e_rho, e_u)
+    b_norm, b_rho, b_u = MEASURED_2X[prec]
+    assert norm_err < b_norm and e_rho < b_rho and e_u < b_u, (norm_err, e_rho, e_u)
 
 
-def test_fp32_state_error_c3_copy(oracle_step):
+@pytest.mark.parametrize("red", ["default", "fp64", "comp"])
+def test_fp32_state_error_c3_copy(oracle_step, red):
     pr, f0, f1 = oracle_step
-    f, rho, ux, uy = _gpu_step(f0, "fp32", "default")
+    f, rho, ux, uy = _gpu_step(f0, "fp32", red)
     norm_err, e_rho, e_u, e_f = _report(pr, f, f1, rho, ux, uy)
-    print(f"fp32: rel max {cases.rel_max_err(f, f1):.3e}, L2 rho {e_rho:.3e}, L2 u/U {e_u:.3e}")
-    assert cases.rel_max_err(f, f1) < 4.0 * pr.Np * U32 * np.sqrt(5) + U32
+    rel = cases.rel_max_err(f, f1)
+    print(f"fp32/{red}: rel max {rel:.3e}, L2 rho {e_rho:.3e}, L2 u/U {e_u:.3e}")
+    assert rel < 4.0 * pr.Np * U32 * np.sqrt(5) + U32
+    assert rel < 5.0e-7 and e_rho < 9.0e-8 and e_u < 4.5e-7, (rel, e_rho, e_u)

@@ -58,8 +58,9 @@ def test_tc_1024_velocities_cavity_kn8(p):
 
 def test_tc_default_selection_and_rejection():
     from paper_2012_13487_gb300 import fedbm as fb
-    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32").info.tensor_cores == 1
-    # explicit FMA tiles, other velocity counts, 16-bit or FP64 state, degree >= 5: FMA form
+    # the untuned default is the FMA form everywhere; tensor cores on request
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32").info.tensor_cores == 0
+    assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32", tc=1).info.tensor_cores == 1
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "fp32", epc=2).info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("gh", 5)), "fp32").info.tensor_cores == 0
     assert cases.solver(cases.cavity(3, 3, 4, velset=("nc", 16)), "bf16").info.tensor_cores == 0
@@ -110,13 +111,24 @@ def test_tc_wait_timeout_reported():
     with pytest.raises(fb.FedbmError) as e:
         s.mass()
     assert e.value.code == fb.FEDBM_ETIMEOUT
+    with pytest.raises(fb.FedbmError) as e:
+        s.moments()
+    assert e.value.code == fb.FEDBM_ETIMEOUT
+    s.close()
+    # every CTA released its tensor memory: the context still runs the
+    # tensor-core form correctly
+    pr, g, f0, f_tc = _pair(c, 3, tc=1)
+    assert g.info.tensor_cores == 1
+    assert cases.rel_max_err(f_tc, pr.run(f0, 3)) < fp32_tol(pr, 15)
 
 
 def test_tc_batch_groups_toggle_bitwise_with_single_solvers():
     from paper_2012_13487_gb300 import fedbm as fb
     cs = [cases.cavity(4, 3, 4, velset=("nc", 16), kn=1.0), cases.couette(5, 2, 2, velset=("nc", 16), kn=2.0),
           cases.cavity(3, 3, 3, velset=("gh", 5))]
-    b = cases.batch(cs, "fp32")
+    # tensor cores requested for the first two cases (two groups), default for the third
+    tcs = [1, 1, 0]
+    b = fb.Batch([fb.case_desc(*cases.descriptors(c, "fp32", tc=t)) for c, t in zip(cs, tcs)])
     prs = [cases.oracle_problem(c) for c in cs]
     f0s = [cases.initial_state(pr, amp=1e-2, seed=21 + j) for j, pr in enumerate(prs)]
     for j, f0 in enumerate(f0s):
@@ -126,7 +138,7 @@ def test_tc_batch_groups_toggle_bitwise_with_single_solvers():
     infos = [b.info(j) for j in range(3)]
     assert [i.tensor_cores for i in infos] == [1, 1, 0]
     for j, c in enumerate(cs):
-        s = cases.solver(c, "fp32")
+        s = cases.solver(c, "fp32", tc=tcs[j])
         s.set_state(f0s[j])
         s.step(5)
         assert np.array_equal(s.state(), got[j])

@@ -1,6 +1,6 @@
 """The FP32 operator tables compiled into the FMA stage kernel
 (csrc/ops_tables.inc) equal the library's runtime operators rounded to FP32,
-bit for bit, for degrees 0..4 (a stale table would change the kernel's
+bit for bit, for degrees 0..5 (a stale table would change the kernel's
 Dr, Ds and LIFT without any other sign)."""
 import os
 import re
@@ -21,7 +21,7 @@ def parse_tables():
     return out
 
 
-@pytest.mark.parametrize("p", range(5))
+@pytest.mark.parametrize("p", range(6))
 def test_ops_table_matches_runtime_operators(p):
     from paper_2012_13487_gb300 import fedbm as fb
     o = fb.fedbm_ref_operators(p)

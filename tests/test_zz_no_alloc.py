@@ -36,6 +36,19 @@ def test_mass_noalloc_matches_fedbm_mass_on_two_calls():
         torch.cuda.synchronize()
         assert int(status.item()) == 0
         assert float(total.item()) == pytest.approx(scale * want, rel=1e-13)
+    # element Jacobians that differ from element to element: the per-element
+    # factor of every node is taken from its own element
+    rng = np.random.default_rng(7)
+    jac_h = (0.5 + rng.random(K)) * (1.0 / 120.0)
+    f_h = f.cpu().numpy()
+    cs_h = colsum.cpu().numpy()
+    want_nu = float(np.sum(jac_h[:, None] * cs_h[None, :] * f_h.sum(axis=-1)))
+    jac_nu = torch.tensor(jac_h, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        fb.fedbm_mass_noalloc(f, jac_nu, colsum, K, Np, Q, total, status, stream)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert float(total.item()) == pytest.approx(want_nu, rel=1e-13)
     # a non-finite value is reported through the status word, then cleared again
     g = f.clone()
     g[2, 1, 3] = float("nan")
