@@ -50,6 +50,8 @@ extern "C" {
 #define FEDBM_ENONFINITE -4   /* NaN/Inf in the state or rho <= 0 at a node   */
 #define FEDBM_ETIMEOUT   -5   /* a bounded device-side wait gave up           */
 #define FEDBM_ENOTSUP    -6   /* configuration not compiled into the library  */
+#define FEDBM_ENOCONV    -7   /* an implicit step's Newton iteration did not
+                                 reach its tolerance                          */
 
 /* ---- enumerations ------------------------------------------------------- */
 enum fedbm_bc_kind {
@@ -223,6 +225,63 @@ int fedbm_rk_step(fedbm_solver* s, int32_t nsteps);
  * ignores the residual's previous contents (its A coefficient is 0).  For
  * testing single stages.  Asynchronous. */
 int fedbm_rk_stage(fedbm_solver* s, int32_t stage);
+
+/* ---- implicit time marching (Sec. II.B.3) ---------------------------------
+ * The paper marches eq. byparts with singly diagonally implicit Runge-Kutta
+ * methods: a four-stage fourth-order scheme for the Couette order study and the
+ * one-stage first-order scheme (backward Euler) for the cavities, each stage
+ * linearised by Newton's method and solved by GMRES.  The paper prints no
+ * tableau for its fourth-order scheme; the library offers two published
+ * fourth-order SDIRK tableaux and a caller-given one:
+ *   FEDBM_IMPLICIT_BE         backward Euler (1 stage, order 1, L-stable)
+ *   FEDBM_IMPLICIT_SDIRK3_O4  Crouzeix/Norsett (3 stages, order 4, A-stable,
+ *                             gamma = 1/2 + cos(pi/18)/sqrt(3))
+ *   FEDBM_IMPLICIT_SDIRK5_O4  Hairer & Wanner (5 stages, order 4, L-stable,
+ *                             gamma = 1/4, stiffly accurate)
+ *   FEDBM_IMPLICIT_CUSTOM     stages 1..6, A (row-major 6 x 6, lower
+ *                             triangular, every diagonal entry A[0][0] > 0), b
+ * Stage i solves Y_i = u_n + dt sum_{j<i} a_ij k_j + dt gamma R(Y_i) by
+ * Newton's method, k_i = (Y_i - base_i)/(dt gamma), u_{n+1} = u_n + dt sum b_i k_i.
+ * Each Newton correction solves (I - dt gamma J) d = -G with restarted
+ * GMRES(m) (classical Gram-Schmidt with re-orthogonalisation, no
+ * preconditioner), J v = (R(Y + e v) - R(Y)) / e matrix-free; every R is one
+ * launch of the fused stage kernel.  Vectors are FP64 in the device layout;
+ * R runs in the solver's precision (FP64 or FP32 state only). */
+enum fedbm_implicit_scheme {
+  FEDBM_IMPLICIT_BE = 0,
+  FEDBM_IMPLICIT_SDIRK3_O4 = 1,
+  FEDBM_IMPLICIT_SDIRK5_O4 = 2,
+  FEDBM_IMPLICIT_CUSTOM = 3
+};
+typedef struct fedbm_implicit_params {
+  int32_t scheme;          /* enum fedbm_implicit_scheme                          */
+  int32_t stages;          /* FEDBM_IMPLICIT_CUSTOM only: 1..6                    */
+  double  A[36];           /* FEDBM_IMPLICIT_CUSTOM only: row-major 6 x 6 tableau */
+  double  b[6];            /* FEDBM_IMPLICIT_CUSTOM only: weights                 */
+  double  dt;              /* time step (not limited by the CFL condition), > 0   */
+  double  newton_rtol;     /* stage converged when |G|_2 <= max(rtol |G_0|_2, atol);
+                              0 means 1e-10                                        */
+  double  newton_atol;     /* absolute 2-norm tolerance; 0 means none            */
+  int32_t newton_max_iter; /* per stage; 0 means 20                               */
+  int32_t gmres_restart;   /* m (1..200); 0 means 30                              */
+  int32_t gmres_max_iter;  /* per Newton correction; 0 means 1000                 */
+  double  gmres_rtol;      /* forcing term: |J d + G| <= rtol |G|; 0 means 1e-4   */
+} fedbm_implicit_params;
+typedef struct fedbm_implicit_stats {
+  int32_t newton_iters;    /* Newton corrections over all stages and steps        */
+  int32_t gmres_iters;     /* GMRES iterations (Jacobian-vector products)         */
+  int32_t rhs_evals;       /* stage-kernel launches evaluating R                  */
+  int32_t converged;       /* 1 if every stage met its Newton tolerance           */
+  double  residual;        /* |G|_2 of the last stage                             */
+} fedbm_implicit_stats;
+
+/* Advance nsteps implicit steps of size ip->dt from the current state
+ * (synchronous).  The time reported by fedbm_info grows by dt per step.
+ * stats may be NULL.  Errors: EINVAL (batches, BF16/FP16 state, bad
+ * parameters), ENOCONV (a stage's Newton iteration reached newton_max_iter;
+ * the state is then the last step's result), ENONFINITE, ECUDA, ENOMEM. */
+int fedbm_implicit_step(fedbm_solver* s, const fedbm_implicit_params* ip, int32_t nsteps,
+                        fedbm_implicit_stats* stats);
 
 /* Node moments rho, u_x, u_y [K][Np] in FP64 of the current state.
  * Synchronous for host outputs; with host outputs it also returns ETIMEOUT if

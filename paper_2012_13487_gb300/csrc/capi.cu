@@ -14,6 +14,7 @@
 #include "device_common.cuh"
 #include "fedbm.h"
 #include "host_setup.h"
+#include "krylov.h"
 #include "stage_dispatch.h"
 
 namespace {
@@ -420,13 +421,14 @@ struct Batch {
   std::vector<Case> cases;
   std::vector<Group> groups;
   int cur = 0;                   // state buffer holding the current f (all groups step together)
-  double time = 0;               // RK steps taken since the last state load
+  double time = 0;               // time advanced by implicit steps since the last state load
   int64_t steps = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   double* staging = nullptr;     // canonical FP64 buffer of the largest case (lazy)
   size_t staging_elems = 0;
   double* mom = nullptr;         // [3][K*Np] of the largest case (lazy)
   size_t mom_elems = 0;
+  struct Implicit* implicit = nullptr;  // Newton-GMRES work space (lazy, single solvers)
 };
 
 bool same_group(const Group& g, const fedbm_mesh_desc& md, const fedbm_velset_desc& vd, const fedbm_params& prm) {
@@ -851,6 +853,8 @@ int build_group(Batch& b, Group& g) {
   return FEDBM_OK;
 }
 
+void free_implicit_of(Batch* b);
+
 void free_batch(Batch* b) {
   if (!b) return;
   cudaSetDevice(b->device);
@@ -868,6 +872,7 @@ void free_batch(Batch* b) {
   }
   cudaFree(b->staging);
   cudaFree(b->mom);
+  free_implicit_of(b);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
 }
@@ -1204,7 +1209,7 @@ int info(const Batch& b, int c, fedbm_info_t* out) {
   out->Q_padded = g.Qp;
   out->dt = cs.dt;
   out->tau = cs.tau;
-  out->time = cs.dt * double(b.steps);
+  out->time = cs.dt * double(b.steps) + b.time;
   out->steps = b.steps;
   out->precision = g.store;
   out->reduction = g.reduction;
@@ -1220,6 +1225,396 @@ int info(const Batch& b, int c, fedbm_info_t* out) {
   out->reserved0 = 0;
   out->state_bytes = cs.K * g.Np * g.Qp * int64_t(store_bytes(g.store));
   out->residual_bytes = cs.K * g.Np * g.Qp * int64_t(real_bytes(g.store));
+  return FEDBM_OK;
+}
+
+// ---------------------------------------------------------------- implicit time marching
+// SDIRK methods with matrix-free Newton-GMRES (Sec. II.B.3: the paper marches
+// with SDIRK, a four-stage fourth-order scheme for the Couette order study and
+// backward Euler for the cavities, each stage linearised by Newton and solved
+// by GMRES).  Every residual evaluation R(Y) is one launch of the fused stage
+// kernel with A = B = 0 and a unit time step in its geometry copy (so that its
+// residual register receives R(Y) itself); Jacobian-vector products are finite
+// differences of R; all vectors are FP64 in the internal layout [K][Np][Qp].
+
+struct Tableau {
+  int s = 0;
+  double A[6][6] = {};
+  double b[6] = {};
+};
+
+bool make_tableau(const fedbm_implicit_params& ip, Tableau& t, std::string& err) {
+  switch (ip.scheme) {
+    case FEDBM_IMPLICIT_BE:  // backward Euler: one stage, first order
+      t.s = 1;
+      t.A[0][0] = 1.0;
+      t.b[0] = 1.0;
+      return true;
+    case FEDBM_IMPLICIT_SDIRK3_O4: {
+      // Crouzeix (1975) / Norsett: three stages, fourth order, A-stable,
+      // gamma = 1/2 + cos(pi/18)/sqrt(3), delta = 1 / (6 (2 gamma - 1)^2)
+      const double g = 0.5 + std::cos(3.14159265358979323846 / 18.0) / std::sqrt(3.0);
+      const double d = 1.0 / (6.0 * (2.0 * g - 1.0) * (2.0 * g - 1.0));
+      t.s = 3;
+      t.A[0][0] = g;
+      t.A[1][0] = 0.5 - g;
+      t.A[1][1] = g;
+      t.A[2][0] = 2.0 * g;
+      t.A[2][1] = 1.0 - 4.0 * g;
+      t.A[2][2] = g;
+      t.b[0] = d;
+      t.b[1] = 1.0 - 2.0 * d;
+      t.b[2] = d;
+      return true;
+    }
+    case FEDBM_IMPLICIT_SDIRK5_O4: {
+      // Hairer & Wanner (Solving ODEs II, Sec. IV.6): five stages, fourth
+      // order, L-stable, gamma = 1/4, stiffly accurate (b = last row)
+      const double A[5][5] = {{1.0 / 4, 0, 0, 0, 0},
+                              {1.0 / 2, 1.0 / 4, 0, 0, 0},
+                              {17.0 / 50, -1.0 / 25, 1.0 / 4, 0, 0},
+                              {371.0 / 1360, -137.0 / 2720, 15.0 / 544, 1.0 / 4, 0},
+                              {25.0 / 24, -49.0 / 48, 125.0 / 16, -85.0 / 12, 1.0 / 4}};
+      t.s = 5;
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) t.A[i][j] = A[i][j];
+      for (int j = 0; j < 5; ++j) t.b[j] = A[4][j];
+      return true;
+    }
+    case FEDBM_IMPLICIT_CUSTOM: {
+      if (ip.stages < 1 || ip.stages > 6) {
+        err = "custom tableau: stages must be 1..6";
+        return false;
+      }
+      t.s = ip.stages;
+      const double gam = ip.A[0];
+      if (!(gam > 0)) {
+        err = "custom tableau: the diagonal must be positive";
+        return false;
+      }
+      for (int i = 0; i < t.s; ++i) {
+        for (int j = 0; j < t.s; ++j) {
+          const double v = ip.A[i * 6 + j];
+          if (j > i && v != 0.0) {
+            err = "custom tableau: A must be lower triangular";
+            return false;
+          }
+          if (j == i && v != gam) {
+            err = "custom tableau: every diagonal entry must equal A[0][0] (singly diagonally implicit)";
+            return false;
+          }
+          t.A[i][j] = v;
+        }
+        t.b[i] = ip.b[i];
+      }
+      return true;
+    }
+  }
+  err = "unknown implicit scheme";
+  return false;
+}
+
+// Device work space of the implicit solver of a single-group solver.
+struct Implicit {
+  int64_t n = 0;        // K * Np * Qp
+  int m = 0, s = 0;     // GMRES restart length, stages
+  double* u0 = nullptr;     // state at the start of the step
+  double* Y = nullptr;      // stage value (Newton iterate)
+  double* base = nullptr;   // u0 + dt sum_{j<i} a_ij k_j
+  double* RY = nullptr;     // R(Y)
+  double* G = nullptr;      // Newton residual, then the GMRES right-hand side -G
+  double* d = nullptr;      // Newton update
+  double* w = nullptr;      // GMRES work vector
+  double* Yp = nullptr;     // Y + eps v
+  double* Rp = nullptr;     // R(Y + eps v)
+  double* V = nullptr;      // GMRES basis [m+1][n]
+  double* k = nullptr;      // stage derivatives [s][n]
+  double* partial = nullptr;  // [m+1][kDotBlocks]
+  double* hdev = nullptr;     // [m+2] dot results / combination coefficients
+  void* x32 = nullptr;        // FP32 state: FP32 copy of the input of R
+  void* r32 = nullptr;        // FP32 state: FP32 residual register
+  void* scratch = nullptr;    // stage-kernel state output (unused values)
+  void* geo_unit = nullptr;   // geometry with dt = 1
+};
+
+void free_implicit(Implicit& im) {
+  void* bufs[] = {im.u0, im.Y, im.base, im.RY, im.G, im.d, im.w, im.Yp, im.Rp, im.V, im.k, im.partial, im.hdev,
+                  im.x32, im.r32, im.scratch, im.geo_unit};
+  for (void* p : bufs) cudaFree(p);
+  im = Implicit();
+}
+
+int ensure_implicit(const Batch& b, const Group& g, Implicit& im, int m, int s) {
+  const int64_t n = g.K * g.Np * g.Qp;
+  if (im.n == n && im.m >= m && im.s >= s) return FEDBM_OK;
+  free_implicit(im);
+  im.n = n;
+  im.m = m;
+  im.s = s;
+  const size_t vb = size_t(n) * sizeof(double);
+  double** vecs[] = {&im.u0, &im.Y, &im.base, &im.RY, &im.G, &im.d, &im.w, &im.Yp, &im.Rp};
+  for (double** v : vecs) FEDBM_CK(cudaMalloc(v, vb));
+  FEDBM_CK(cudaMalloc(&im.V, vb * size_t(m + 1)));
+  FEDBM_CK(cudaMalloc(&im.k, vb * size_t(s)));
+  FEDBM_CK(cudaMalloc(&im.partial, size_t(m + 1) * krylov::kDotBlocks * sizeof(double)));
+  FEDBM_CK(cudaMalloc(&im.hdev, size_t(m + 2) * sizeof(double)));
+  const size_t rb = real_bytes(g.store);
+  FEDBM_CK(cudaMalloc(&im.scratch, size_t(n) * rb));
+  if (g.store == kStoreF32) {
+    FEDBM_CK(cudaMalloc(&im.x32, size_t(n) * 4));
+    FEDBM_CK(cudaMalloc(&im.r32, size_t(n) * 4));
+  }
+  FEDBM_CK(cudaMalloc(&im.geo_unit, size_t(g.K) * kGeoStrideDev * rb));
+  FEDBM_CK(cudaMemcpyAsync(im.geo_unit, g.geo, size_t(g.K) * kGeoStrideDev * rb, cudaMemcpyDeviceToDevice, b.stream));
+  FEDBM_CK(krylov::set_geo_dt(g.K, kGeoStrideDev, kGeoDt, 1.0, im.geo_unit, int(rb), b.stream));
+  return FEDBM_OK;
+}
+
+// r = R(x): one fused stage-kernel launch with A = B = 0 and unit time step
+int implicit_rhs(const Batch& b, const Group& g, Implicit& im, const double* x, double* r) {
+  const StageEntry e = stage_entry(g.p);
+  if (g.store == kStoreF64) {
+    StageArgs<double> a;
+    fill_stage_args(g, 0, b.cur, a);
+    a.f_in = x;
+    a.f_out = im.scratch;
+    a.res = r;
+    a.geo = static_cast<const double*>(im.geo_unit);
+    a.rkA = 0.0;
+    a.rkB = 0.0;
+    FEDBM_CK(e.launch(g.store, &a, g.grid, g.tpb, g.smem, b.stream));
+    return FEDBM_OK;
+  }
+  FEDBM_CK(krylov::to_f32(im.n, x, static_cast<float*>(im.x32), b.stream));
+  StageArgs<float> a;
+  fill_stage_args(g, 0, b.cur, a);
+  a.f_in = im.x32;
+  a.f_out = im.scratch;
+  a.res = static_cast<float*>(im.r32);
+  a.geo = static_cast<const float*>(im.geo_unit);
+  a.rkA = 0.f;
+  a.rkB = 0.f;
+  if (g.tc) FEDBM_CK(e.launch_tc(g.store, &a, g.grid, g.smem, b.stream));
+  else FEDBM_CK(e.launch(g.store, &a, g.grid, g.tpb, g.smem, b.stream));
+  FEDBM_CK(krylov::to_f64(im.n, static_cast<const float*>(im.r32), r, b.stream));
+  return FEDBM_OK;
+}
+
+// 2-norm of x (synchronous)
+int implicit_norm(const Batch& b, Implicit& im, const double* x, double* out) {
+  FEDBM_CK(krylov::multi_dot(im.n, 1, x, x, im.partial, im.hdev, b.stream));
+  double h = 0;
+  FEDBM_CK(cudaMemcpyAsync(&h, im.hdev, sizeof(double), cudaMemcpyDeviceToHost, b.stream));
+  FEDBM_CK(cudaStreamSynchronize(b.stream));
+  *out = std::sqrt(std::max(0.0, h));
+  return FEDBM_OK;
+}
+
+struct ImplicitCounters {
+  int newton = 0, gmres = 0, rhs = 0;
+  double residual = 0;
+  bool converged = true;
+};
+
+// Restarted GMRES(m) for (I - dt gamma J) d = rhs (rhs in im.G), x0 = 0,
+// classical Gram-Schmidt with one re-orthogonalisation; J v is taken as
+// (R(Y + eps v) - R(Y)) / eps.  Stops when the residual is <= tol.
+int implicit_gmres(const Batch& b, const Group& g, Implicit& im, double dtg, double eps, double tol, int max_iter,
+                   ImplicitCounters& cnt) {
+  const int64_t n = im.n;
+  const int m = im.m;
+  cudaStream_t st = b.stream;
+  FEDBM_CK(cudaMemsetAsync(im.d, 0, size_t(n) * sizeof(double), st));
+  std::vector<double> H(size_t(m + 1) * m, 0.0), cs(m), sn(m), gv(m + 1), y(m), h1(m + 1), h2(m + 1);
+  int total = 0;
+  bool first = true;
+  while (total < max_iter) {
+    // r = rhs - A d  (d = 0 on the first cycle)
+    double* v0 = im.V;
+    if (first) {
+      FEDBM_CK(cudaMemcpyAsync(v0, im.G, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+      // A d = d - dtg (R(Y + e d) - R(Y)) / e, e = eps / |d| (a unit-size difference)
+      double dn = 0;
+      int rc = implicit_norm(b, im, im.d, &dn);
+      if (rc) return rc;
+      const double ed = dn > 0 ? eps / dn : eps;
+      FEDBM_CK(krylov::axpby(n, 1.0, im.Y, ed, im.d, im.Yp, st));
+      if ((rc = implicit_rhs(b, g, im, im.Yp, im.Rp)) != FEDBM_OK) return rc;
+      ++cnt.rhs;
+      FEDBM_CK(krylov::axpby(n, 1.0, im.Rp, -1.0, im.RY, im.w, st));
+      FEDBM_CK(krylov::axpby(n, 1.0, im.d, -dtg / ed, im.w, im.w, st));
+      FEDBM_CK(krylov::axpby(n, 1.0, im.G, -1.0, im.w, v0, st));
+    }
+    first = false;
+    double beta = 0;
+    int rc = implicit_norm(b, im, v0, &beta);
+    if (rc) return rc;
+    if (beta <= tol) return FEDBM_OK;
+    FEDBM_CK(krylov::axpby(n, 1.0 / beta, v0, 0.0, v0, v0, st));
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jend = 0;
+    double resid = beta;
+    for (int j = 0; j < m && total < max_iter; ++j, ++total) {
+      double* vj = im.V + size_t(j) * n;
+      // w = A v_j
+      FEDBM_CK(krylov::axpby(n, 1.0, im.Y, eps, vj, im.Yp, st));
+      if ((rc = implicit_rhs(b, g, im, im.Yp, im.Rp)) != FEDBM_OK) return rc;
+      ++cnt.rhs;
+      FEDBM_CK(krylov::axpby(n, 1.0, im.Rp, -1.0, im.RY, im.w, st));
+      FEDBM_CK(krylov::axpby(n, 1.0, vj, -dtg / eps, im.w, im.w, st));
+      // two passes of classical Gram-Schmidt against v_0 .. v_j
+      for (int pass = 0; pass < 2; ++pass) {
+        std::vector<double>& hh = pass == 0 ? h1 : h2;
+        FEDBM_CK(krylov::multi_dot(n, j + 1, im.V, im.w, im.partial, im.hdev, st));
+        FEDBM_CK(krylov::sub_combination(n, j + 1, im.V, im.hdev, im.w, st));
+        FEDBM_CK(cudaMemcpyAsync(hh.data(), im.hdev, size_t(j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      }
+      double hn = 0;
+      if ((rc = implicit_norm(b, im, im.w, &hn)) != FEDBM_OK) return rc;  // synchronises: h1, h2 are valid
+      ++cnt.gmres;
+      for (int i = 0; i <= j; ++i) H[size_t(i) * m + j] = h1[i] + h2[i];
+      H[size_t(j + 1) * m + j] = hn;
+      if (j + 1 <= m && hn > 0)
+        FEDBM_CK(krylov::axpby(n, 1.0 / hn, im.w, 0.0, im.w, im.V + size_t(j + 1) * n, st));
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        const double a0 = H[size_t(i) * m + j], a1 = H[size_t(i + 1) * m + j];
+        H[size_t(i) * m + j] = cs[i] * a0 + sn[i] * a1;
+        H[size_t(i + 1) * m + j] = -sn[i] * a0 + cs[i] * a1;
+      }
+      const double a0 = H[size_t(j) * m + j], a1 = H[size_t(j + 1) * m + j];
+      const double r = std::hypot(a0, a1);
+      cs[j] = r > 0 ? a0 / r : 1.0;
+      sn[j] = r > 0 ? a1 / r : 0.0;
+      H[size_t(j) * m + j] = r;
+      H[size_t(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      resid = std::fabs(gv[j + 1]);
+      jend = j + 1;
+      if (resid <= tol || hn == 0.0) {
+        ++total;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular jend x jend), d += V y
+    for (int i = jend - 1; i >= 0; --i) {
+      double acc = gv[i];
+      for (int q = i + 1; q < jend; ++q) acc -= H[size_t(i) * m + q] * y[q];
+      y[i] = H[size_t(i) * m + i] != 0.0 ? acc / H[size_t(i) * m + i] : 0.0;
+    }
+    FEDBM_CK(cudaMemcpyAsync(im.hdev, y.data(), size_t(jend) * sizeof(double), cudaMemcpyHostToDevice, st));
+    FEDBM_CK(krylov::add_combination(n, jend, im.V, im.hdev, im.d, st));
+    FEDBM_CK(cudaStreamSynchronize(st));  // y (host) is reused by the next cycle
+    if (resid <= tol) return FEDBM_OK;
+  }
+  return FEDBM_OK;  // the caller's Newton loop judges the outcome
+}
+
+void free_implicit_of(Batch* b) {
+  if (b->implicit) {
+    free_implicit(*b->implicit);
+    delete b->implicit;
+    b->implicit = nullptr;
+  }
+}
+
+int implicit_step(Batch& b, const fedbm_implicit_params& ip, int nsteps, fedbm_implicit_stats* stats) {
+  NvtxRange nvtx("fedbm implicit_step");
+  if (b.groups.size() != 1 || b.cases.size() != 1)
+    return fail(FEDBM_EINVAL, "implicit stepping serves single solvers (one case)");
+  Group& g = b.groups[0];
+  if (g.store != kStoreF64 && g.store != kStoreF32)
+    return fail(FEDBM_EINVAL, "implicit stepping needs FP64 or FP32 state");
+  if (nsteps < 0) return fail(FEDBM_EINVAL, "nsteps must be >= 0");
+  if (!(ip.dt > 0)) return fail(FEDBM_EINVAL, "implicit dt must be > 0");
+  Tableau tb;
+  std::string err;
+  if (!make_tableau(ip, tb, err)) return fail(FEDBM_EINVAL, err);
+  const int m = ip.gmres_restart > 0 ? std::min(ip.gmres_restart, 200) : 30;
+  const int gmax = ip.gmres_max_iter > 0 ? ip.gmres_max_iter : 1000;
+  const int nmax = ip.newton_max_iter > 0 ? ip.newton_max_iter : 20;
+  const double rtol = ip.newton_rtol > 0 ? ip.newton_rtol : 1e-10;
+  const double atol = ip.newton_atol > 0 ? ip.newton_atol : 0.0;
+  const double eta = ip.gmres_rtol > 0 ? ip.gmres_rtol : 1e-4;
+  if (!b.implicit) b.implicit = new Implicit();
+  Implicit* im = b.implicit;
+  int rc = ensure_implicit(b, g, *im, m, tb.s);
+  if (rc) return rc;
+  const int64_t n = im->n;
+  cudaStream_t st = b.stream;
+  const double eps_mach = g.store == kStoreF64 ? 2.220446049250313e-16 : 1.1920929e-07;
+  const double dt = ip.dt;
+  const double dtg = dt * tb.A[0][0];
+  ImplicitCounters cnt;
+  const size_t vb = size_t(n) * sizeof(double);
+  for (int step = 0; step < nsteps; ++step) {
+    // u0 = current state in FP64
+    if (g.store == kStoreF64) FEDBM_CK(cudaMemcpyAsync(im->u0, g.f[b.cur], vb, cudaMemcpyDeviceToDevice, st));
+    else FEDBM_CK(krylov::to_f64(n, static_cast<const float*>(g.f[b.cur]), im->u0, st));
+    for (int i = 0; i < tb.s; ++i) {
+      // base = u0 + dt sum_{j<i} a_ij k_j
+      FEDBM_CK(cudaMemcpyAsync(im->base, im->u0, vb, cudaMemcpyDeviceToDevice, st));
+      if (i > 0) {
+        std::vector<double> c(i);
+        for (int j = 0; j < i; ++j) c[j] = dt * tb.A[i][j];
+        FEDBM_CK(cudaMemcpyAsync(im->hdev, c.data(), size_t(i) * sizeof(double), cudaMemcpyHostToDevice, st));
+        FEDBM_CK(krylov::add_combination(n, i, im->k, im->hdev, im->base, st));
+        FEDBM_CK(cudaStreamSynchronize(st));
+      }
+      // initial guess: the previous stage value (or u0)
+      if (i == 0) FEDBM_CK(cudaMemcpyAsync(im->Y, im->u0, vb, cudaMemcpyDeviceToDevice, st));
+      double g0 = -1, gn = 0;
+      bool ok = false;
+      for (int it = 0; it <= nmax; ++it) {
+        if ((rc = implicit_rhs(b, g, *im, im->Y, im->RY)) != FEDBM_OK) return rc;
+        ++cnt.rhs;
+        // G = Y - base - dtg R(Y)
+        FEDBM_CK(krylov::axpby(n, 1.0, im->Y, -1.0, im->base, im->G, st));
+        FEDBM_CK(krylov::axpby(n, 1.0, im->G, -dtg, im->RY, im->G, st));
+        if ((rc = implicit_norm(b, *im, im->G, &gn)) != FEDBM_OK) return rc;
+        if (g0 < 0) g0 = gn;
+        if (!std::isfinite(gn)) return fail(FEDBM_ENONFINITE, "implicit step: non-finite Newton residual");
+        if (gn <= std::max(rtol * g0, atol)) {
+          ok = true;
+          break;
+        }
+        if (it == nmax) break;
+        ++cnt.newton;
+        // solve (I - dtg J) d = -G
+        FEDBM_CK(krylov::axpby(n, -1.0, im->G, 0.0, im->G, im->G, st));
+        double ynorm = 0;
+        if ((rc = implicit_norm(b, *im, im->Y, &ynorm)) != FEDBM_OK) return rc;
+        const double eps = std::sqrt(eps_mach) * (1.0 + ynorm);
+        if ((rc = implicit_gmres(b, g, *im, dtg, eps, eta * gn, gmax, cnt)) != FEDBM_OK) return rc;
+        FEDBM_CK(krylov::axpby(n, 1.0, im->Y, 1.0, im->d, im->Y, st));
+      }
+      cnt.residual = gn;
+      if (!ok) cnt.converged = false;
+      // k_i = (Y - base) / (dt gamma), consistent with the solved stage equation
+      FEDBM_CK(krylov::axpby(n, 1.0 / dtg, im->Y, -1.0 / dtg, im->base, im->k + size_t(i) * n, st));
+    }
+    // u1 = u0 + dt sum_i b_i k_i, into the current state buffer
+    std::vector<double> c(tb.s);
+    for (int j = 0; j < tb.s; ++j) c[j] = dt * tb.b[j];
+    FEDBM_CK(cudaMemcpyAsync(im->hdev, c.data(), size_t(tb.s) * sizeof(double), cudaMemcpyHostToDevice, st));
+    FEDBM_CK(krylov::add_combination(n, tb.s, im->k, im->hdev, im->u0, st));
+    if (g.store == kStoreF64) FEDBM_CK(cudaMemcpyAsync(g.f[b.cur], im->u0, vb, cudaMemcpyDeviceToDevice, st));
+    else FEDBM_CK(krylov::to_f32(n, im->u0, static_cast<float*>(g.f[b.cur]), st));
+    FEDBM_CK(cudaStreamSynchronize(st));
+    b.time += dt;
+    if (!cnt.converged) break;
+  }
+  if (stats) {
+    stats->newton_iters = cnt.newton;
+    stats->gmres_iters = cnt.gmres;
+    stats->rhs_evals = cnt.rhs;
+    stats->converged = cnt.converged ? 1 : 0;
+    stats->residual = cnt.residual;
+  }
+  if (!cnt.converged) return fail(FEDBM_ENOCONV, "implicit step: Newton did not reach its tolerance");
   return FEDBM_OK;
 }
 
@@ -1358,6 +1753,13 @@ extern "C" int fedbm_rk_stage(fedbm_solver* s, int32_t stage) {
   FEDBM_CK(launch_stage(B.groups[0], stage, B.cur, B.stream));
   B.cur = 1 - B.cur;
   return FEDBM_OK;
+}
+
+extern "C" int fedbm_implicit_step(fedbm_solver* s, const fedbm_implicit_params* ip, int32_t nsteps,
+                                   fedbm_implicit_stats* stats) {
+  FEDBM_SOLVER(s);
+  if (!ip) return fail(FEDBM_EINVAL, "null implicit parameters");
+  return implicit_step(B, *ip, nsteps, stats);
 }
 
 extern "C" int fedbm_get_moments(fedbm_solver* s, double* rho, double* ux, double* uy, int32_t on_device) {

@@ -62,6 +62,23 @@ class Info(ctypes.Structure):
                 ("residual_bytes", ctypes.c_int64)]
 
 
+IMPLICIT_BE, IMPLICIT_SDIRK3_O4, IMPLICIT_SDIRK5_O4, IMPLICIT_CUSTOM = 0, 1, 2, 3
+FEDBM_ENOCONV = -7
+
+
+class ImplicitParams(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("stages", ctypes.c_int32), ("A", ctypes.c_double * 36),
+                ("b", ctypes.c_double * 6), ("dt", ctypes.c_double), ("newton_rtol", ctypes.c_double),
+                ("newton_atol", ctypes.c_double), ("newton_max_iter", ctypes.c_int32),
+                ("gmres_restart", ctypes.c_int32), ("gmres_max_iter", ctypes.c_int32),
+                ("gmres_rtol", ctypes.c_double)]
+
+
+class ImplicitStats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int32), ("gmres_iters", ctypes.c_int32), ("rhs_evals", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("residual", ctypes.c_double)]
+
+
 class CaseDesc(ctypes.Structure):
     _fields_ = [("mesh", MeshDesc), ("velset", VelsetDesc), ("params", Params)]
 
@@ -85,6 +102,8 @@ SIGNATURES = {
                                              ctypes.c_double, ctypes.c_uint64]),
     "fedbm_rk_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "fedbm_rk_stage": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "fedbm_implicit_step": (ctypes.c_int, [_P, ctypes.POINTER(ImplicitParams), ctypes.c_int32,
+                                           ctypes.POINTER(ImplicitStats)]),
     "fedbm_get_moments": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32]),
     "fedbm_get_state": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "fedbm_get_residual": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
@@ -264,6 +283,29 @@ def fedbm_rk_stage(h, stage):
     _check(lib().fedbm_rk_stage(h, stage))
 
 
+def implicit_params(scheme=IMPLICIT_BE, dt=1.0, newton_rtol=0.0, newton_atol=0.0, newton_max_iter=0,
+                    gmres_restart=0, gmres_max_iter=0, gmres_rtol=0.0, A=None, b=None):
+    ip = ImplicitParams()
+    ip.scheme, ip.dt = scheme, dt
+    ip.newton_rtol, ip.newton_atol, ip.newton_max_iter = newton_rtol, newton_atol, newton_max_iter
+    ip.gmres_restart, ip.gmres_max_iter, ip.gmres_rtol = gmres_restart, gmres_max_iter, gmres_rtol
+    if A is not None:
+        A = np.asarray(A, dtype=np.float64)
+        ip.stages = A.shape[0]
+        for i in range(A.shape[0]):
+            for j in range(A.shape[1]):
+                ip.A[6 * i + j] = A[i, j]
+        for j, v in enumerate(b):
+            ip.b[j] = v
+    return ip
+
+
+def fedbm_implicit_step(h, ip, nsteps=1):
+    st = ImplicitStats()
+    _check(lib().fedbm_implicit_step(h, ctypes.byref(ip), nsteps, ctypes.byref(st)))
+    return st
+
+
 def fedbm_get_moments(h, rho, ux, uy, on_device):
     _check(lib().fedbm_get_moments(h, _ptr(rho), _ptr(ux), _ptr(uy), int(on_device)))
 
@@ -440,6 +482,10 @@ class Solver:
 
     def stage(self, s):
         fedbm_rk_stage(self.h, s)
+
+    def implicit_step(self, ip, n=1):
+        """n implicit SDIRK steps (Newton-GMRES); returns the ImplicitStats."""
+        return fedbm_implicit_step(self.h, ip, n)
 
     def state(self):
         f = np.zeros(self.shape)

@@ -73,7 +73,11 @@ def advection_error(N, p, precision, T=0.1):
 
 @pytest.mark.parametrize("p", [1, 2, 3])
 def test_fp32_state_converges_at_p_plus_1_transient(p):
-    ns = (4, 8, 16)
+    # measured on the GB300 (max error / max w): p=1 4.95e-2, 1.25e-2, 3.33e-3;
+    # p=2 1.98e-2, 2.33e-3, 3.69e-4 (N = 4, 8, 16); at p=3 and N=16 the FP32
+    # rounding of ~2,500 stage updates (2.5e-5) matches the discretisation
+    # error, so p=3 is checked on N = 2, 4, 8
+    ns = (4, 8, 16) if p < 3 else (2, 4, 8)
     e32 = [advection_error(n, p, "fp32") for n in ns]
     e64 = [advection_error(n, p, "fp64") for n in ns]
     print("fp32", p, e32, "fp64", e64)
@@ -84,10 +88,14 @@ def test_fp32_state_converges_at_p_plus_1_transient(p):
 
 
 def test_bf16_state_converges_at_p_plus_1_until_its_storage_floor():
-    e = [advection_error(n, 1, "bf16") for n in (4, 8)]
-    e64 = [advection_error(n, 1, "fp64") for n in (4, 8)]
+    # Each LSRK stage changes the deviation by dt B res, which at N = 8 (p = 1)
+    # is about a tenth of a BF16 unit of the stored deviation: the update is
+    # rounded away and the state falls behind (measured: 4.0e-2 against the
+    # FP64 discrete solution's 1.25e-2).  On the coarse meshes, where the
+    # stage increments exceed the BF16 unit, the BF16 state follows the FP64
+    # discrete solution and its order.
+    e = [advection_error(n, 1, "bf16") for n in (2, 4)]
+    e64 = [advection_error(n, 1, "fp64") for n in (2, 4)]
     print("bf16 p=1", e, "fp64", e64)
     assert np.log2(e[0] / e[1]) > 2 - 0.6, e
-    # within the BF16 storage floor (2^-9 of the 0.1 deviation per encoding,
-    # a random walk over the steps) of the FP64 discrete solution
-    assert np.all(np.abs(np.array(e) - np.array(e64)) < 0.25 * np.array(e64)), (e, e64)
+    assert np.all(np.abs(np.array(e) - np.array(e64)) < 0.02 * np.array(e64)), (e, e64)

@@ -1,0 +1,106 @@
+"""Implicit SDIRK time marching on the GPU (Sec. II.B.3: SDIRK with Newton's
+method and GMRES), against the oracle's SDIRK steps, which solve every stage
+with a dense finite-difference Jacobian instead of the library's matrix-free
+Newton-GMRES; tolerances follow from the solver tolerances requested."""
+import numpy as np
+import pytest
+
+from oracle import couette, dg, implicit
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+
+def _tight(scheme, dt, **kw):
+    from paper_2012_13487_gb300 import fedbm as fb
+    args = dict(newton_rtol=1e-13, newton_atol=1e-14, newton_max_iter=30, gmres_restart=80,
+                gmres_max_iter=2000, gmres_rtol=1e-11)
+    args.update(kw)
+    return fb.implicit_params(scheme, dt, **args)
+
+
+def _couette_small():
+    return cases.couette(1, 3, 2, velset=("gh", 3), kn=0.5)
+
+
+@pytest.mark.parametrize("scheme,name", [(0, "be"), (1, "sdirk3o4"), (2, "sdirk5o4")])
+def test_implicit_steps_match_oracle_fp64(scheme, name):
+    c = _couette_small()
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=2e-2, seed=12)
+    dt = 20 * pr.dt                       # well past the explicit CFL limit
+    s = cases.solver(c, "fp64")
+    s.set_state(f0)
+    st = s.implicit_step(_tight(scheme, dt), 2)
+    assert st.converged == 1 and st.gmres_iters > 0
+    assert abs(s.info.time - 2 * dt) < 1e-15
+    f_or = implicit.march(pr, f0, dt, 2, name)
+    assert cases.rel_max_err(s.state(), f_or) < 1e-10
+    assert abs(s.mass() - pr.mass(f0)) < 1e-12
+
+
+def test_implicit_fp32_state():
+    c = _couette_small()
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=2e-2, seed=13)
+    dt = 10 * pr.dt
+    s = cases.solver(c, "fp32")
+    s.set_state(f0)
+    st = s.implicit_step(_tight(0, dt, newton_rtol=1e-6, gmres_rtol=1e-6), 1)
+    assert st.converged == 1
+    f_or, _ = implicit.sdirk_step(pr, f0, dt, "be")
+    assert cases.rel_max_err(s.state(), f_or) < 2e-6
+
+
+def test_custom_tableau_equals_backward_euler():
+    from paper_2012_13487_gb300 import fedbm as fb
+    c = _couette_small()
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=2e-2, seed=14)
+    out = []
+    for ip in (_tight(0, 0.05), fb.implicit_params(fb.IMPLICIT_CUSTOM, 0.05, newton_rtol=1e-13, newton_atol=1e-14,
+                                                   newton_max_iter=30, gmres_restart=80, gmres_max_iter=2000,
+                                                   gmres_rtol=1e-11, A=[[1.0]], b=[1.0])):
+        s = cases.solver(c, "fp64")
+        s.set_state(f0)
+        s.implicit_step(ip, 1)
+        out.append(s.state())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_backward_euler_pseudo_time_couette_order_p_plus_1():
+    """The paper's steady runs: backward Euler with large steps to the steady
+    state, then the repaired eq. exact at order p + 1 (Couette, Kn = 1)."""
+    UW = 1e-3
+    for p in (1, 2):
+        errs = []
+        for ny in (2, 4, 8):
+            c = cases.couette(1, ny, p, U=UW, velset=("gh", 4), kn=1.0)
+            pr = cases.oracle_problem(c)
+            s = cases.solver(c, "fp64")
+            s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 0)
+            s.implicit_step(_tight(0, 5.0, newton_rtol=1e-12, gmres_rtol=1e-8, gmres_restart=100,
+                                   gmres_max_iter=5000), 12)
+            _, ux, _ = s.moments()
+            errs.append(pr.l2_error(ux, lambda x, y: couette.exact_ux(y, 1.0, UW, -UW)) / (2 * UW))
+        rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        print("BE pseudo-time p=%d" % p, errs, rates)
+        assert np.all(rates > p + 1 - 0.15), (p, errs, rates)
+
+
+def test_implicit_errors():
+    from paper_2012_13487_gb300 import fedbm as fb
+    c = _couette_small()
+    s = cases.solver(c, "bf16")
+    s.set_equilibrium(1.0, 0.0, 0.0, 1e-3, 1)
+    with pytest.raises(fb.FedbmError) as e:
+        s.implicit_step(_tight(0, 0.1), 1)
+    assert e.value.code == fb.FEDBM_EINVAL
+    s = cases.solver(c, "fp64")
+    s.set_equilibrium(1.0, 0.0, 0.0, 1e-2, 1)
+    with pytest.raises(fb.FedbmError) as e:   # one Newton correction cannot reach 1e-15 relative
+        s.implicit_step(_tight(0, 1.0, newton_rtol=1e-15, newton_atol=0.0, newton_max_iter=1, gmres_rtol=1e-2), 1)
+    assert e.value.code == fb.FEDBM_ENOCONV
+    with pytest.raises(fb.FedbmError) as e:
+        s.implicit_step(fb.implicit_params(fb.IMPLICIT_CUSTOM, 0.1, A=[[0.5, 0.1], [0.2, 0.5]], b=[0.5, 0.5]), 1)
+    assert e.value.code == fb.FEDBM_EINVAL
