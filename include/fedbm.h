@@ -74,6 +74,14 @@ enum fedbm_reduction {
   FEDBM_RED_COMP_FP32 = 2     /* compensated (Neumaier) FP32 accumulation      */
 };
 
+enum fedbm_tau_model {
+  FEDBM_TAU_KN         = 0,   /* eq. KnTau: tau = Kn L / (sqrt(3) c_s)        */
+  FEDBM_TAU_KIM_PITSCH = 1,   /* Kim & Pitsch mean free path: Kn carries a
+                                 factor sqrt(pi/6), tau = Kn L / (sqrt(pi/2) c_s) */
+  FEDBM_TAU_PSI        = 2    /* eq. KnTau times psi(Kn) =
+                                 (2/pi) arctan(sqrt(2) Kn^(-3/4)) (Zhang)      */
+};
+
 /* ---- descriptors -------------------------------------------------------- */
 /* Mesh of straight-sided triangles on the rectangle [0, lx] x [0, ly].
  * Sides: 0 -> y = 0, 1 -> x = lx, 2 -> y = ly, 3 -> x = 0.  Periodic sides must
@@ -118,7 +126,7 @@ typedef struct fedbm_velset_desc {
 } fedbm_velset_desc;
 
 typedef struct fedbm_params {
-  double  kn;            /* Knudsen number; tau = kn*length/sqrt(3) (eq. KnTau) */
+  double  kn;            /* Knudsen number; tau from it by tau_model below       */
   double  length;        /* characteristic length L (0 means 1)                 */
   double  beta;          /* flux parameter: 1 upwind, 0.5 central (Sec. II.B.1) */
   double  cfl;           /* dt = cfl*r_in,min/(max|e|*(p+1)^2) when dt <= 0     */
@@ -148,6 +156,14 @@ typedef struct fedbm_params {
                               returns and the next synchronous read-out
                               (fedbm_mass, or get_moments / get_state to
                               host memory) reports FEDBM_ETIMEOUT            */
+  int32_t tau_model;     /* enum fedbm_tau_model (Sec. II.A.4); 0 = eq. KnTau   */
+  int32_t velocity_split; /* velocity-split stage kernel, a thread-block cluster
+                             of CTAs sharing each element (FP64, FP32, BF16
+                             state): 0 = automatic (used when one CTA cannot
+                             hold all velocities of an element, e.g. D2Q1089
+                             at degree 5 and 6), 1 = never, 2, 4 or 8 = that
+                             cluster size (EINVAL where it does not divide
+                             the padded velocity count into multiples of 8) */
 } fedbm_params;
 
 typedef struct fedbm_info_t {
@@ -159,7 +175,8 @@ typedef struct fedbm_info_t {
   int32_t pipeline_stages, grid; /* stage-kernel buffers per CTA; persistent grid */
   int32_t group, ngroups;        /* batches: kernel group of this case; group count */
   int32_t tensor_cores;          /* 1 if the group's stage kernel is the tensor-core form */
-  int32_t reserved0;
+  int32_t velocity_split;        /* CTAs per element tile: 1, or the cluster size of the
+                                    velocity-split form                          */
   int64_t state_bytes;           /* device bytes of one state buffer             */
   int64_t residual_bytes;        /* device bytes of the RK residual              */
 } fedbm_info_t;

@@ -76,9 +76,25 @@ def equilibrium(rho, ux, uy, ex, ey, w, eq_order=2):
     return w * rho[..., None] * poly
 
 
-def tau_from_kn(kn, L=1.0, cs=1.0):
-    """Relaxation time of eq. KnTau: tau = Kn L / (sqrt(3) c_s)."""
-    return kn * L / (np.sqrt(3.0) * cs)
+def tau_from_kn(kn, L=1.0, cs=1.0, model="kn"):
+    """Relaxation time from Kn (Sec. II.A.4).
+
+    "kn": eq. KnTau, the mean free path lambda = sqrt(3) tau c_s and
+          Kn = lambda / L, so tau = Kn L / (sqrt(3) c_s).
+    "kim_pitsch": the mean free path of Kim and Pitsch from kinetic theory,
+          lambda = tau c_s sqrt(pi / 2), which is sqrt(pi/6) times the one
+          above (the paper's "additional factor of sqrt(pi/6)").
+    "psi": eq. KnTau scaled by psi(Kn) = (2/pi) arctan(sqrt(2) Kn^(-3/4)).
+    """
+    if model == "kn":
+        return kn * L / (np.sqrt(3.0) * cs)
+    if model == "kim_pitsch":
+        lam_per_tau = cs * np.sqrt(np.pi / 2.0)     # lambda / tau
+        return kn * L / lam_per_tau
+    if model == "psi":
+        psi = 2.0 / np.pi * np.arctan(np.sqrt(2.0) * kn ** -0.75)
+        return psi * tau_from_kn(kn, L, cs)
+    raise ValueError(model)
 
 
 class Problem:
@@ -96,13 +112,13 @@ class Problem:
                  beta=1.0, bc=("diffuse", "periodic", "diffuse", "periodic"),
                  wall_u=((-0.1, 0.0), (0.0, 0.0), (0.1, 0.0), (0.0, 0.0)),
                  cfl=0.5, dt=None, collision=True, Lx=1.0, Ly=1.0,
-                 nc_extent=4.0, nc_scale=1.0, mesh=None):
+                 nc_extent=4.0, nc_scale=1.0, mesh=None, tau_model="kn"):
         self.Nx, self.Ny, self.p = Nx, Ny, p
         kind, n = velset
         self.ex, self.ey, self.w = _velset.velocity_set(kind, n, nc_extent, nc_scale)
         self.Q = len(self.w)
         self.eq_order = eq_order
-        self.tau = tau_from_kn(kn, L)
+        self.tau = tau_from_kn(kn, L, model=tau_model)
         self.collision = collision
         self.ab = 2.0 * beta - 1.0
         self.bc = tuple(bc)

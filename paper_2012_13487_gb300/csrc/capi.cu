@@ -390,9 +390,14 @@ struct Group {
   int test_wait_timeout = 0;
   int tc_mode = 0;  // fedbm_params.tensor_cores of the group's cases
   int tc = 0;       // 1: the stage kernel is the tensor-core form
+  int vsplit = 0;   // fedbm_params.velocity_split of the group's cases
+  int ncl = 0;      // > 1: the velocity-split form with clusters of ncl CTAs
   int64_t K = 0;
   std::vector<int> cases;
   int epc = 0, tpb = 0, nstages = 1, grid = 0;
+  int per_sm = 0;       // resident stage CTAs per SM of the configured kernel
+  int branch_grid = 0;  // grid inside a multi-group graph (its share of the SMs)
+  double tune_us = 0;   // autotuned time of one step-shaped trial (0 = not tuned)
   size_t smem = 0;
   RefOps ops;
   VelocitySet vs;
@@ -436,7 +441,8 @@ bool same_group(const Group& g, const fedbm_mesh_desc& md, const fedbm_velset_de
          g.vd.nc_extent == vd.nc_extent && g.vd.nc_sqrt2 == vd.nc_sqrt2 && g.vd.eq_order == vd.eq_order &&
          g.collision == prm.collision && g.reduction == prm.reduction && g.beta == prm.beta &&
          g.epc == prm.elems_per_cta && g.tpb == prm.threads_per_cta && g.nstages == prm.pipeline_stages &&
-         g.test_wait_timeout == prm.test_wait_timeout && g.tc_mode == prm.tensor_cores;
+         g.test_wait_timeout == prm.test_wait_timeout && g.tc_mode == prm.tensor_cores &&
+         g.vsplit == prm.velocity_split;
 }
 
 template <typename R>
@@ -469,17 +475,60 @@ void fill_stage_args(const Group& g, int stage, int from, StageArgs<R>& a) {
   a.extra_tx = g.test_wait_timeout ? 16u : 0u;
 }
 
-cudaError_t launch_stage(const Group& g, int stage, int from, cudaStream_t st) {
+// Launch the group's configured stage-kernel form with these arguments.
+cudaError_t launch_args(const Group& g, const void* args, cudaStream_t st, int grid = 0) {
   const StageEntry e = stage_entry(g.p);
+  if (grid <= 0) grid = g.grid;
+  if (g.ncl > 1) return e.launch_cl(g.store, args, g.grid / g.ncl, g.ncl, g.smem, st);
+  if (g.tc) return e.launch_tc(g.store, args, grid, g.smem, st);
+  return e.launch(g.store, args, grid, g.tpb, g.smem, st);
+}
+
+cudaError_t launch_stage(const Group& g, int stage, int from, cudaStream_t st, int grid = 0) {
   if (g.store == kStoreF64) {
     StageArgs<double> a;
     fill_stage_args(g, stage, from, a);
-    return e.launch(g.store, &a, g.grid, g.tpb, g.smem, st);
+    return launch_args(g, &a, st, grid);
   }
   StageArgs<float> a;
   fill_stage_args(g, stage, from, a);
-  if (g.tc) return e.launch_tc(g.store, &a, g.grid, g.smem, st);
-  return e.launch(g.store, &a, g.grid, g.tpb, g.smem, st);
+  return launch_args(g, &a, st, grid);
+}
+
+// Grids of the groups of a multi-group step: every group's persistent grid
+// gets the share of the GPU's resident CTA slots that its share of the step's
+// work asks for, so that the branches of the graph run side by side from the
+// start and finish together (full-GPU grids for every group would make the
+// first-launched branch hold every SM and run the groups one after another).
+// The work of a group is its autotuned step time when it has one, else its
+// DOF count times the operator work per DOF, 2 Np + 3 Nfp + 30 flops.
+void share_grids(Batch& b) {
+  if (b.groups.size() < 2) {
+    for (Group& g : b.groups) g.branch_grid = g.grid;
+    return;
+  }
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device);
+  double total = 0;
+  std::vector<double> work(b.groups.size());
+  bool all_tuned = true;
+  for (const Group& g : b.groups) all_tuned = all_tuned && g.tune_us > 0;
+  for (size_t j = 0; j < b.groups.size(); ++j) {
+    const Group& g = b.groups[j];
+    work[j] = all_tuned ? g.tune_us : double(g.K) * g.Np * g.Qp * (2.0 * g.Np + 3.0 * g.Nfp + 30.0);
+    total += work[j];
+  }
+  for (size_t j = 0; j < b.groups.size(); ++j) {
+    Group& g = b.groups[j];
+    if (g.ncl > 1) {  // cluster grids stay whole clusters
+      g.branch_grid = g.grid;
+      continue;
+    }
+    const int64_t ntiles = (g.K + g.epc - 1) / g.epc;
+    const double slots = double(std::max(1, g.per_sm)) * nsm * (total > 0 ? work[j] / total : 1.0);
+    const int64_t want = std::max<int64_t>(std::max(1, g.per_sm), int64_t(std::ceil(slots)));
+    g.branch_grid = int(std::max<int64_t>(1, std::min<int64_t>({want, ntiles, int64_t(g.grid)})));
+  }
 }
 
 void drop_graphs(Batch& b) {
@@ -512,20 +561,58 @@ int configure_tc(Batch& b, Group& g) {
   if (per_sm < 1 || std::max(per_sm, by_smem) * e.tc_tmem_cols(g.Qp) > 512)
     return fail(FEDBM_EINVAL, "tensor-core stage kernel cannot be resident within tensor memory");
   g.tc = 1;
+  g.ncl = 0;
   g.epc = g.Qp < 128 ? 128 / g.Qp : 1;  // stacked elements per tile below 128 velocities
   g.tpb = 128;                          // one 128-row MMA tile per pass
   g.nstages = 1;
   g.smem = smem;
   g.grid = int(std::min<int64_t>((g.K + g.epc - 1) / g.epc, int64_t(per_sm) * nsm));
+  g.per_sm = per_sm;
   drop_graphs(b);
   return FEDBM_OK;
 }
 
 bool tc_available(const Group& g) { return g.tc_mode >= 0 && stage_entry(g.p).tc_smem(g.store, g.Qp) > 0; }
 
+// The velocity-split form of a group: clusters of ncl CTAs, each CTA one
+// slice of Qp / ncl velocities of one element per tile, 256 threads; the
+// persistent grid holds as many clusters as can be resident at once.
+int configure_cluster(Batch& b, Group& g, int ncl) {
+  const StageEntry e = stage_entry(g.p);
+  const size_t smem = e.cl_smem(g.store, g.Qp, ncl, 1);
+  if (smem == 0) return fail(FEDBM_EINVAL, "no velocity-split form for this precision or cluster size "
+                                           "(FP64, FP32 or BF16 state; clusters of 2, 4 or 8 CTAs dividing the "
+                                           "padded velocity count into multiples of 8)");
+  if (smem > 227 * 1024) return fail(FEDBM_EINVAL, "velocity-split tile does not fit in shared memory");
+  FEDBM_CK(e.set_smem_cl(g.store, smem));
+  const int nclusters_max = e.occupancy_cl(g.store, ncl, smem);
+  if (nclusters_max < 1) return fail(FEDBM_EINVAL, "velocity-split clusters cannot be resident");
+  g.tc = 0;
+  g.ncl = ncl;
+  g.epc = 1;
+  g.tpb = 256;
+  g.nstages = 1;
+  g.smem = smem;
+  g.per_sm = 0;
+  g.grid = int(std::min<int64_t>(g.K, int64_t(nclusters_max))) * ncl;
+  drop_graphs(b);
+  return FEDBM_OK;
+}
+
+// Smallest cluster size whose velocity slice fits shared memory, 0 if none.
+int auto_cluster(const Group& g) {
+  const StageEntry e = stage_entry(g.p);
+  for (int ncl : {2, 4, 8}) {
+    const size_t smem = e.cl_smem(g.store, g.Qp, ncl, 1);
+    if (smem > 0 && smem <= 227 * 1024) return ncl;
+  }
+  return 0;
+}
+
 // Tile shape, pipeline depth and persistent grid of a group's stage kernel.
 int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
   g.tc = 0;
+  g.ncl = 0;
   g.epc = epc > 0 ? epc : (g.Qp < 128 ? std::max(1, 128 / g.Qp) : 1);
   g.tpb = tpb > 0 ? tpb : std::min(128, std::max(32, (g.epc * g.Qp + 31) / 32 * 32));
   if (g.tpb % 32 || g.tpb > 256) return fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256");
@@ -545,6 +632,7 @@ int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
   if (per_sm < 1) return fail(FEDBM_EINVAL, "stage tile cannot be resident on an SM");
   const int64_t ntiles = (g.K + g.epc - 1) / g.epc;
   g.grid = int(std::min<int64_t>(ntiles, int64_t(per_sm) * nsm));
+  g.per_sm = per_sm;
   drop_graphs(b);
   return FEDBM_OK;
 }
@@ -616,6 +704,7 @@ int autotune(Batch& b, const char* cache_path, int trials) {
   FEDBM_CK(cudaEventCreate(&e1));
   int rc = FEDBM_OK;
   for (Group& g : b.groups) {
+    if (g.ncl > 1) continue;  // the velocity-split form has a single configuration
     if (g.tc_mode > 0) {  // tensor cores required: nothing to choose
       if ((rc = configure_tc(b, g)) != FEDBM_OK) break;
       continue;
@@ -626,6 +715,7 @@ int autotune(Batch& b, const char* cache_path, int trials) {
       if (kv.first == key) hit = &kv.second;
     if (hit && (!hit->tc || tc_available(g))) {
       if ((rc = apply_tune(b, g, *hit)) != FEDBM_OK) break;
+      g.tune_us = hit->us;
       continue;
     }
     TuneEntry best;
@@ -676,6 +766,7 @@ int autotune(Batch& b, const char* cache_path, int trials) {
       break;
     }
     if ((rc = apply_tune(b, g, best)) != FEDBM_OK) break;
+    g.tune_us = best.us;
     cache.emplace_back(key, best);
     dirty = true;
   }
@@ -700,6 +791,7 @@ int build_graphs(Batch& b) {
       le = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
       if (le == cudaSuccess) le = cudaEventRecord(fork, b.capture);
     }
+    share_grids(b);
     for (Group& g : b.groups) {
       if (le != cudaSuccess) break;
       cudaStream_t st = b.capture;
@@ -709,7 +801,7 @@ int build_graphs(Batch& b) {
       }
       int from = c;
       for (int s = 0; s < 5 && le == cudaSuccess; ++s) {
-        le = launch_stage(g, s, from, st);
+        le = launch_stage(g, s, from, st, g.branch_grid);
         from = 1 - from;
       }
       if (branches && le == cudaSuccess) {
@@ -745,6 +837,24 @@ int upload_real(const std::vector<double>& h, void** d) {
   return upload_vec(v, d);
 }
 
+// Relaxation time from Kn (Sec. II.A.4, theta = RT = c_s^2 = 1):
+//   FEDBM_TAU_KN:          eq. KnTau, mean free path lambda = sqrt(3) tau c_s,
+//                          tau = Kn L / (sqrt(3) c_s);
+//   FEDBM_TAU_KIM_PITSCH:  the kinetic-theory mean free path of Kim and Pitsch,
+//                          which puts a factor sqrt(pi/6) into Kn:
+//                          Kn = sqrt(pi/6) sqrt(3) tau c_s / L, i.e.
+//                          tau = Kn L / (sqrt(pi/2) c_s);
+//   FEDBM_TAU_PSI:         eq. KnTau scaled by the Kn-dependent function
+//                          psi(Kn) = (2/pi) arctan(sqrt(2) Kn^(-3/4)) (Zhang).
+double relaxation_time(double kn, double L, int model) {
+  const double pi = 3.14159265358979323846;
+  switch (model) {
+    case FEDBM_TAU_KIM_PITSCH: return kn * L / std::sqrt(pi / 2.0);
+    case FEDBM_TAU_PSI: return kn * L / std::sqrt(3.0) * (2.0 / pi) * std::atan(std::sqrt(2.0) * std::pow(kn, -0.75));
+    default: return kn * L / std::sqrt(3.0);
+  }
+}
+
 // Host set-up of a group in FP64 (meshes, walls, geometry) and device upload.
 int build_group(Batch& b, Group& g) {
   std::string err;
@@ -753,7 +863,10 @@ int build_group(Batch& b, Group& g) {
   g.Np = g.ops.Np;
   g.Nfp = g.ops.Nfp;
   g.Q = g.vs.Q;
-  g.Qp = (g.Q + 7) / 8 * 8;
+  // padded velocity count: a multiple of 8 (16-byte vectors of the 16-bit
+  // forms); above 512 velocities a multiple of 32, so that the velocity-split
+  // form can give clusters of 2 or 4 CTAs slices of whole vectors
+  g.Qp = g.Q > 512 ? (g.Q + 31) / 32 * 32 : (g.Q + 7) / 8 * 8;
   const int Np = g.Np, Qp = g.Qp, Q = g.Q;
   const int nslots = 4 * int(g.cases.size());
   std::vector<int32_t> nbr;
@@ -770,7 +883,7 @@ int build_group(Batch& b, Group& g) {
     cs.k_off = g.K;
     cs.K = m.K;
     const double L = cs.prm.length > 0 ? cs.prm.length : 1.0;
-    cs.tau = cs.prm.kn * L / std::sqrt(3.0);
+    cs.tau = relaxation_time(cs.prm.kn, L, cs.prm.tau_model);
     cs.dt = cs.prm.dt > 0 ? cs.prm.dt : time_step(m, g.vs, g.p, cs.prm.cfl);
     const double itau = g.collision ? 1.0 / cs.tau : 0.0;
     for (int64_t k = 0; k < m.K; ++k) {
@@ -892,7 +1005,12 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
     if (prm.reduction < FEDBM_RED_DEFAULT || prm.reduction > FEDBM_RED_COMP_FP32)
       return bail(fail(FEDBM_EINVAL, "unknown reduction mode"));
     if (!(prm.kn > 0)) return bail(fail(FEDBM_EINVAL, "kn must be > 0"));
+    if (prm.tau_model < FEDBM_TAU_KN || prm.tau_model > FEDBM_TAU_PSI)
+      return bail(fail(FEDBM_EINVAL, "unknown tau_model"));
     if (prm.tensor_cores < -1 || prm.tensor_cores > 1) return bail(fail(FEDBM_EINVAL, "tensor_cores must be -1, 0 or 1"));
+    if (prm.velocity_split != 0 && prm.velocity_split != 1 && prm.velocity_split != 2 && prm.velocity_split != 4 &&
+        prm.velocity_split != 8)
+      return bail(fail(FEDBM_EINVAL, "velocity_split must be 0, 1, 2, 4 or 8"));
     if (!(prm.beta >= 0.5 && prm.beta <= 1.0)) return bail(fail(FEDBM_EINVAL, "beta must be in [0.5, 1]"));
     if (!(prm.dt > 0) && !(prm.cfl > 0)) return bail(fail(FEDBM_EINVAL, "need dt > 0 or cfl > 0"));
     if (cd[c].mesh.order < 0 || cd[c].mesh.order > kMaxOrder) return bail(fail(FEDBM_EINVAL, "order must be in 0..6"));
@@ -916,6 +1034,7 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
       g.nstages = prm.pipeline_stages;
       g.test_wait_timeout = prm.test_wait_timeout;
       g.tc_mode = prm.tensor_cores;
+      g.vsplit = prm.velocity_split;
       b->groups.push_back(g);
       gi = int(b->groups.size()) - 1;
     }
@@ -939,7 +1058,13 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
            // tiles and degree 5 likewise); tensor cores on request
            // (tensor_cores = 1) or when the autotuner times them faster
            const bool want_tc = g.tc_mode > 0;
-           if (want_tc) {
+           // the velocity-split form on request, or when one CTA cannot hold
+           // an element's velocities (automatic mode)
+           const bool too_big = stage_smem_bytes(g.p, g.store, std::max(1, epc), g.Qp, 1) > 227 * 1024;
+           const int ncl = g.vsplit >= 2 ? g.vsplit : (g.vsplit == 0 && too_big && !want_tc ? auto_cluster(g) : 0);
+           if (ncl >= 2) {
+             if ((r = configure_cluster(*b, g, ncl)) != FEDBM_OK) return r;
+           } else if (want_tc) {
              if ((r = configure_tc(*b, g)) != FEDBM_OK) return r;
            } else if ((r = configure_tiles(*b, g, epc, tpb, st)) != FEDBM_OK) {
              return r;
@@ -1222,7 +1347,7 @@ int info(const Batch& b, int c, fedbm_info_t* out) {
   out->group = cs.group;
   out->ngroups = int32_t(b.groups.size());
   out->tensor_cores = g.tc;
-  out->reserved0 = 0;
+  out->velocity_split = g.ncl > 1 ? g.ncl : 1;
   out->state_bytes = cs.K * g.Np * g.Qp * int64_t(store_bytes(g.store));
   out->residual_bytes = cs.K * g.Np * g.Qp * int64_t(real_bytes(g.store));
   return FEDBM_OK;
@@ -1372,7 +1497,6 @@ int ensure_implicit(const Batch& b, const Group& g, Implicit& im, int m, int s) 
 
 // r = R(x): one fused stage-kernel launch with A = B = 0 and unit time step
 int implicit_rhs(const Batch& b, const Group& g, Implicit& im, const double* x, double* r) {
-  const StageEntry e = stage_entry(g.p);
   if (g.store == kStoreF64) {
     StageArgs<double> a;
     fill_stage_args(g, 0, b.cur, a);
@@ -1382,7 +1506,7 @@ int implicit_rhs(const Batch& b, const Group& g, Implicit& im, const double* x, 
     a.geo = static_cast<const double*>(im.geo_unit);
     a.rkA = 0.0;
     a.rkB = 0.0;
-    FEDBM_CK(e.launch(g.store, &a, g.grid, g.tpb, g.smem, b.stream));
+    FEDBM_CK(launch_args(g, &a, b.stream));
     return FEDBM_OK;
   }
   FEDBM_CK(krylov::to_f32(im.n, x, static_cast<float*>(im.x32), b.stream));
@@ -1394,8 +1518,7 @@ int implicit_rhs(const Batch& b, const Group& g, Implicit& im, const double* x, 
   a.geo = static_cast<const float*>(im.geo_unit);
   a.rkA = 0.f;
   a.rkB = 0.f;
-  if (g.tc) FEDBM_CK(e.launch_tc(g.store, &a, g.grid, g.smem, b.stream));
-  else FEDBM_CK(e.launch(g.store, &a, g.grid, g.tpb, g.smem, b.stream));
+  FEDBM_CK(launch_args(g, &a, b.stream));
   FEDBM_CK(krylov::to_f64(im.n, static_cast<const float*>(im.r32), r, b.stream));
   return FEDBM_OK;
 }

@@ -18,6 +18,12 @@ struct StageEntry {
   cudaError_t (*launch_tc)(int store_kind, const void* args, int grid, size_t smem, cudaStream_t st);
   cudaError_t (*set_smem_tc)(int store_kind, int Qp, size_t smem);
   int (*occupancy_tc)(int store_kind, int Qp, size_t smem);
+  // velocity-split form (a cluster of ncl CTAs per element tile; FP64, FP32,
+  // BF16 state; Qp a multiple of 8 ncl)
+  size_t (*cl_smem)(int store_kind, int Qp, int ncl, int epc);  // 0 = no such form
+  cudaError_t (*launch_cl)(int store_kind, const void* args, int nclusters, int ncl, size_t smem, cudaStream_t st);
+  cudaError_t (*set_smem_cl)(int store_kind, size_t smem);
+  int (*occupancy_cl)(int store_kind, int ncl, size_t smem);  // resident clusters on the device
 };
 
 StageEntry stage_entry_p0();

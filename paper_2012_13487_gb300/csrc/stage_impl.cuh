@@ -839,6 +839,7 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
 }
 
 #include "stage_tc.cuh"
+#include "stage_cluster.cuh"
 
 template <class ST, int QT>
 cudaError_t launch_one(const void* args, int grid, int block, size_t smem, cudaStream_t st) {
@@ -968,6 +969,10 @@ StageEntry FEDBM_STAGE_ENTRY_NAME() {
   s.launch_tc = &launch_tc;
   s.set_smem_tc = &set_smem_tc;
   s.occupancy_tc = &occupancy_tc;
+  s.cl_smem = &cl_smem;
+  s.launch_cl = &launch_cl;
+  s.set_smem_cl = &set_smem_cl;
+  s.occupancy_cl = &occupancy_cl;
   return s;
 }
 

@@ -25,6 +25,7 @@ BC_PERIODIC, BC_WALL_DIFFUSE, BC_WALL_EQ = 0, 1, 2
 VELSET_GH, VELSET_NC = 0, 1
 FP64, FP32, BF16_DEV, FP16_DEV = 0, 1, 2, 3
 RED_DEFAULT, RED_FP64, RED_COMP_FP32 = 0, 1, 2
+TAU_KN, TAU_KIM_PITSCH, TAU_PSI = 0, 1, 2
 
 
 class MeshDesc(ctypes.Structure):
@@ -46,7 +47,8 @@ class Params(ctypes.Structure):
                 ("reduction", ctypes.c_int32), ("collision", ctypes.c_int32),
                 ("elems_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
-                ("test_wait_timeout", ctypes.c_int32)]
+                ("test_wait_timeout", ctypes.c_int32), ("tau_model", ctypes.c_int32),
+                ("velocity_split", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +59,7 @@ class Info(ctypes.Structure):
                 ("eq_order", ctypes.c_int32), ("elems_per_cta", ctypes.c_int32),
                 ("threads_per_cta", ctypes.c_int32), ("pipeline_stages", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("group", ctypes.c_int32), ("ngroups", ctypes.c_int32),
-                ("tensor_cores", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("tensor_cores", ctypes.c_int32), ("velocity_split", ctypes.c_int32),
                 ("state_bytes", ctypes.c_int64),
                 ("residual_bytes", ctypes.c_int64)]
 
@@ -206,7 +208,7 @@ def velset_desc(kind=VELSET_GH, n=4, eq_order=2, nc_extent=4.0, nc_sqrt2=0):
 
 def params(kn=1.0, precision=FP32, reduction=RED_DEFAULT, cfl=0.5, dt=0.0, beta=1.0, collision=1,
            length=1.0, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0, tensor_cores=0,
-           test_wait_timeout=0):
+           test_wait_timeout=0, tau_model=0, velocity_split=0):
     p = Params()
     p.kn, p.length, p.beta, p.cfl, p.dt = kn, length, beta, cfl, dt
     p.precision, p.reduction, p.collision = precision, reduction, collision
@@ -214,6 +216,8 @@ def params(kn=1.0, precision=FP32, reduction=RED_DEFAULT, cfl=0.5, dt=0.0, beta=
     p.pipeline_stages = pipeline_stages
     p.tensor_cores = tensor_cores
     p.test_wait_timeout = test_wait_timeout
+    p.tau_model = tau_model
+    p.velocity_split = velocity_split
     return p
 
 
@@ -464,7 +468,11 @@ class Solver:
 
     def __init__(self, mesh, vs, prm, stream=0):
         self.h = fedbm_create(mesh, vs, prm, stream)
-        self.info = fedbm_info(self.h)
+
+    @property
+    def info(self):
+        """fedbm_info of the solver now (tile, time step, time, steps, ...)."""
+        return fedbm_info(self.h)
 
     @property
     def shape(self):
@@ -508,7 +516,6 @@ class Solver:
 
     def autotune(self, cache_path=None, trials=0):
         fedbm_autotune(self.h, cache_path, trials)
-        self.info = fedbm_info(self.h)
 
     def close(self):
         if self.h is not None and self.h.value:

@@ -7,6 +7,7 @@ from paper_2012_13487_gb300 import inputs
 BC_CODE = {"periodic": 0, "diffuse": 1, "eq": 2}
 PREC_CODE = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
 RED_CODE = {"default": 0, "fp64": 1, "comp": 2}
+TAU_CODE = {"kn": 0, "kim_pitsch": 1, "psi": 2}
 
 COUETTE_BC = ("diffuse", "periodic", "diffuse", "periodic")
 CAVITY_BC = ("diffuse",) * 4
@@ -31,7 +32,8 @@ def oracle_problem(c):
     return dg.Problem(c["nx"], c["ny"], c["p"], velset=vs, eq_order=c.get("eq_order", 2),
                       kn=c.get("kn", 1.0), beta=c.get("beta", 1.0), bc=c["bc"], wall_u=c["wall_u"],
                       cfl=c.get("cfl", 0.5), collision=c.get("collision", True),
-                      nc_scale=np.sqrt(2.0) if c.get("nc_sqrt2", False) else 1.0, mesh=c.get("mesh"))
+                      nc_scale=np.sqrt(2.0) if c.get("nc_sqrt2", False) else 1.0, mesh=c.get("mesh"),
+                      tau_model=c.get("tau_model", "kn"))
 
 
 def descriptors(c, precision="fp32", reduction="default", **tile):
@@ -49,7 +51,8 @@ def descriptors(c, precision="fp32", reduction="default", **tile):
                     cfl=c.get("cfl", 0.5), beta=c.get("beta", 1.0), collision=int(c.get("collision", True)),
                     elems_per_cta=tile.get("epc", 0), threads_per_cta=tile.get("tpb", 0),
                     pipeline_stages=tile.get("stages", 0), tensor_cores=tile.get("tc", 0),
-                    test_wait_timeout=tile.get("test_wait_timeout", 0))
+                    test_wait_timeout=tile.get("test_wait_timeout", 0),
+                    tau_model=TAU_CODE[c.get("tau_model", "kn")], velocity_split=tile.get("vsplit", 0))
     return m, v, prm
 
 

@@ -74,10 +74,10 @@ def advection_error(N, p, precision, T=0.1):
 @pytest.mark.parametrize("p", [1, 2, 3])
 def test_fp32_state_converges_at_p_plus_1_transient(p):
     # measured on the GB300 (max error / max w): p=1 4.95e-2, 1.25e-2, 3.33e-3;
-    # p=2 1.98e-2, 2.33e-3, 3.69e-4 (N = 4, 8, 16); at p=3 and N=16 the FP32
-    # rounding of ~2,500 stage updates (2.5e-5) matches the discretisation
-    # error, so p=3 is checked on N = 2, 4, 8
-    ns = (4, 8, 16) if p < 3 else (2, 4, 8)
+    # p=2 1.98e-2, 2.33e-3, 3.69e-4 (N = 4, 8, 16); p=3 4.75e-3, 3.29e-4 (N = 4,
+    # 8).  At p=3 and N=16 the FP32 rounding of ~2,500 stage updates (2.5e-5)
+    # matches the discretisation error, so p=3 is checked on N = 4, 8
+    ns = (4, 8, 16) if p < 3 else (4, 8)
     e32 = [advection_error(n, p, "fp32") for n in ns]
     e64 = [advection_error(n, p, "fp64") for n in ns]
     print("fp32", p, e32, "fp64", e64)
@@ -87,15 +87,21 @@ def test_fp32_state_converges_at_p_plus_1_transient(p):
     assert np.all(np.abs(np.array(e32) - np.array(e64)) < 0.02 * np.array(e64)), (e32, e64)
 
 
-def test_bf16_state_converges_at_p_plus_1_until_its_storage_floor():
-    # Each LSRK stage changes the deviation by dt B res, which at N = 8 (p = 1)
-    # is about a tenth of a BF16 unit of the stored deviation: the update is
-    # rounded away and the state falls behind (measured: 4.0e-2 against the
-    # FP64 discrete solution's 1.25e-2).  On the coarse meshes, where the
-    # stage increments exceed the BF16 unit, the BF16 state follows the FP64
-    # discrete solution and its order.
-    e = [advection_error(n, 1, "bf16") for n in (2, 4)]
-    e64 = [advection_error(n, 1, "fp64") for n in (2, 4)]
-    print("bf16 p=1", e, "fp64", e64)
-    assert np.log2(e[0] / e[1]) > 2 - 0.6, e
-    assert np.all(np.abs(np.array(e) - np.array(e64)) < 0.02 * np.array(e64)), (e, e64)
+@pytest.mark.parametrize("p", [1, 2])
+def test_bf16_state_follows_fp64_until_its_increments_round_away(p):
+    """BF16 deviation storage on the same transient.  Each LSRK stage changes
+    the stored deviation by dt B res, a fixed fraction of a BF16 unit that
+    shrinks with dt: on N = 4 the increments exceed the unit and the BF16
+    state matches the FP64 discrete solution (error within 1 %), while on
+    N = 8 (p = 1) they are about a tenth of the unit, are rounded away, and
+    the state falls behind (measured: 4.0e-2 against FP64's 1.25e-2).  So the
+    BF16 form shows no order beyond N = 4 on this problem; a reduced-precision
+    state limits refinement studies, not the throughput runs."""
+    e = advection_error(4, p, "bf16")
+    e64 = advection_error(4, p, "fp64")
+    print("bf16 p=%d N=4" % p, e, "fp64", e64)
+    assert abs(e - e64) < 0.01 * e64, (e, e64)
+    if p == 1:
+        e8, e8_64 = advection_error(8, 1, "bf16"), advection_error(8, 1, "fp64")
+        print("bf16 p=1 N=8", e8, "fp64", e8_64)
+        assert e8 > 2 * e8_64            # the rounding-away of small increments, as stated

@@ -13,8 +13,10 @@ pytestmark = pytest.mark.gpu
 
 def _tight(scheme, dt, **kw):
     from paper_2012_13487_gb300 import fedbm as fb
-    args = dict(newton_rtol=1e-13, newton_atol=1e-14, newton_max_iter=30, gmres_restart=80,
-                gmres_max_iter=2000, gmres_rtol=1e-11)
+    # the stage equations are solved to |G| <= 1e-12 |G_0| (or 1e-13 absolute,
+    # near the FP64 rounding of dt R), so the results agree to ~1e-11 relative
+    args = dict(newton_rtol=1e-12, newton_atol=1e-13, newton_max_iter=30, gmres_restart=80,
+                gmres_max_iter=2000, gmres_rtol=1e-10)
     args.update(kw)
     return fb.implicit_params(scheme, dt, **args)
 
@@ -46,7 +48,8 @@ def test_implicit_fp32_state():
     dt = 10 * pr.dt
     s = cases.solver(c, "fp32")
     s.set_state(f0)
-    st = s.implicit_step(_tight(0, dt, newton_rtol=1e-6, gmres_rtol=1e-6), 1)
+    # FP32 residuals: Newton to the FP32 rounding level of G
+    st = s.implicit_step(_tight(0, dt, newton_rtol=1e-5, newton_atol=1e-6, gmres_rtol=1e-5), 1)
     assert st.converged == 1
     f_or, _ = implicit.sdirk_step(pr, f0, dt, "be")
     assert cases.rel_max_err(s.state(), f_or) < 2e-6
@@ -58,9 +61,9 @@ def test_custom_tableau_equals_backward_euler():
     pr = cases.oracle_problem(c)
     f0 = cases.initial_state(pr, amp=2e-2, seed=14)
     out = []
-    for ip in (_tight(0, 0.05), fb.implicit_params(fb.IMPLICIT_CUSTOM, 0.05, newton_rtol=1e-13, newton_atol=1e-14,
+    for ip in (_tight(0, 0.05), fb.implicit_params(fb.IMPLICIT_CUSTOM, 0.05, newton_rtol=1e-12, newton_atol=1e-13,
                                                    newton_max_iter=30, gmres_restart=80, gmres_max_iter=2000,
-                                                   gmres_rtol=1e-11, A=[[1.0]], b=[1.0])):
+                                                   gmres_rtol=1e-10, A=[[1.0]], b=[1.0])):
         s = cases.solver(c, "fp64")
         s.set_state(f0)
         s.implicit_step(ip, 1)
@@ -79,8 +82,9 @@ def test_backward_euler_pseudo_time_couette_order_p_plus_1():
             pr = cases.oracle_problem(c)
             s = cases.solver(c, "fp64")
             s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 0)
-            s.implicit_step(_tight(0, 5.0, newton_rtol=1e-12, gmres_rtol=1e-8, gmres_restart=100,
-                                   gmres_max_iter=5000), 12)
+            st = s.implicit_step(_tight(0, 5.0, newton_rtol=1e-9, newton_atol=1e-12, gmres_rtol=1e-6,
+                                        gmres_restart=100, gmres_max_iter=5000), 12)
+            print("ny=%d p=%d: Newton %d GMRES %d" % (ny, p, st.newton_iters, st.gmres_iters))
             _, ux, _ = s.moments()
             errs.append(pr.l2_error(ux, lambda x, y: couette.exact_ux(y, 1.0, UW, -UW)) / (2 * UW))
         rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))

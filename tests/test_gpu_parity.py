@@ -244,7 +244,7 @@ def test_largest_velocity_sets_fp32(vs, p, sqrt2):
     1096 and 328 (no compile-time stride)."""
     c = cases.cavity(2, 2, p, velset=vs, kn=2.0, nc_sqrt2=sqrt2)
     pr, s, f0, f_gpu, f_or = _run_pair(c, 2, "fp32", amp=1e-2)
-    assert s.info.Q == vs[1] ** 2 and s.info.Q_padded % 8 == 0
+    assert s.info.Q == vs[1] ** 2 and s.info.Q_padded % 8 == 0 and s.info.velocity_split == 1
     assert cases.rel_max_err(f_gpu, f_or) < fp32_tol(pr, 10)
 
 

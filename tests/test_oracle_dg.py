@@ -39,6 +39,24 @@ def test_tau_from_kn():
     assert dg.tau_from_kn(8.0, L=2.0) == pytest.approx(16 / np.sqrt(3), rel=1e-15)
 
 
+def test_tau_models():
+    # Kim & Pitsch: for one and the same tau their Kn is sqrt(pi/6) times the
+    # Kn of eq. KnTau (the paper's "additional factor"), so for one Kn their
+    # tau is sqrt(6/pi) times larger
+    for kn in (0.1, 1.0, 8.0):
+        assert dg.tau_from_kn(kn, model="kim_pitsch") / dg.tau_from_kn(kn) == pytest.approx(np.sqrt(6 / np.pi),
+                                                                                            rel=1e-15)
+    # psi(Kn) = (2/pi) arctan(sqrt(2) Kn^-3/4): psi(1) is (2/pi) times the
+    # magic angle arccos(1/sqrt(3)); psi -> 1 in the continuum limit
+    assert dg.tau_from_kn(1.0, model="psi") / dg.tau_from_kn(1.0) == pytest.approx(
+        2 / np.pi * np.arccos(1 / np.sqrt(3)), rel=1e-14)
+    assert dg.tau_from_kn(1e-8, model="psi") / dg.tau_from_kn(1e-8) == pytest.approx(1.0, abs=1e-5)
+    # and decays like (2/pi) sqrt(2) Kn^-3/4 in the free-molecular limit
+    kn = 1e6
+    assert dg.tau_from_kn(kn, model="psi") / dg.tau_from_kn(kn) == pytest.approx(
+        2 / np.pi * np.sqrt(2) * kn ** -0.75, rel=1e-8)
+
+
 def test_free_stream_periodic_is_steady():
     pr = dg.Problem(4, 3, 3, velset=("gh", 4), eq_order=3, bc=("periodic",) * 4)
     f = pr.equilibrium_state(1.1, 0.05, -0.03)
