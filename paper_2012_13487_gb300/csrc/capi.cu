@@ -396,7 +396,6 @@ struct Group {
   std::vector<int> cases;
   int epc = 0, tpb = 0, nstages = 1, grid = 0;
   int per_sm = 0;       // resident stage CTAs per SM of the configured kernel
-  int branch_grid = 0;  // grid inside a multi-group graph (its share of the SMs)
   double tune_us = 0;   // autotuned time of one step-shaped trial (0 = not tuned)
   size_t smem = 0;
   RefOps ops;
@@ -495,41 +494,6 @@ cudaError_t launch_stage(const Group& g, int stage, int from, cudaStream_t st, i
   return launch_args(g, &a, st, grid);
 }
 
-// Grids of the groups of a multi-group step: every group's persistent grid
-// gets the share of the GPU's resident CTA slots that its share of the step's
-// work asks for, so that the branches of the graph run side by side from the
-// start and finish together (full-GPU grids for every group would make the
-// first-launched branch hold every SM and run the groups one after another).
-// The work of a group is its autotuned step time when it has one, else its
-// DOF count times the operator work per DOF, 2 Np + 3 Nfp + 30 flops.
-void share_grids(Batch& b) {
-  if (b.groups.size() < 2) {
-    for (Group& g : b.groups) g.branch_grid = g.grid;
-    return;
-  }
-  int nsm = 152;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device);
-  double total = 0;
-  std::vector<double> work(b.groups.size());
-  bool all_tuned = true;
-  for (const Group& g : b.groups) all_tuned = all_tuned && g.tune_us > 0;
-  for (size_t j = 0; j < b.groups.size(); ++j) {
-    const Group& g = b.groups[j];
-    work[j] = all_tuned ? g.tune_us : double(g.K) * g.Np * g.Qp * (2.0 * g.Np + 3.0 * g.Nfp + 30.0);
-    total += work[j];
-  }
-  for (size_t j = 0; j < b.groups.size(); ++j) {
-    Group& g = b.groups[j];
-    if (g.ncl > 1) {  // cluster grids stay whole clusters
-      g.branch_grid = g.grid;
-      continue;
-    }
-    const int64_t ntiles = (g.K + g.epc - 1) / g.epc;
-    const double slots = double(std::max(1, g.per_sm)) * nsm * (total > 0 ? work[j] / total : 1.0);
-    const int64_t want = std::max<int64_t>(std::max(1, g.per_sm), int64_t(std::ceil(slots)));
-    g.branch_grid = int(std::max<int64_t>(1, std::min<int64_t>({want, ntiles, int64_t(g.grid)})));
-  }
-}
 
 void drop_graphs(Batch& b) {
   for (int c = 0; c < 2; ++c)
@@ -791,7 +755,6 @@ int build_graphs(Batch& b) {
       le = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
       if (le == cudaSuccess) le = cudaEventRecord(fork, b.capture);
     }
-    share_grids(b);
     for (Group& g : b.groups) {
       if (le != cudaSuccess) break;
       cudaStream_t st = b.capture;
@@ -801,7 +764,7 @@ int build_graphs(Batch& b) {
       }
       int from = c;
       for (int s = 0; s < 5 && le == cudaSuccess; ++s) {
-        le = launch_stage(g, s, from, st, g.branch_grid);
+        le = launch_stage(g, s, from, st);
         from = 1 - from;
       }
       if (branches && le == cudaSuccess) {

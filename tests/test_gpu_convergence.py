@@ -87,21 +87,20 @@ def test_fp32_state_converges_at_p_plus_1_transient(p):
     assert np.all(np.abs(np.array(e32) - np.array(e64)) < 0.02 * np.array(e64)), (e32, e64)
 
 
-@pytest.mark.parametrize("p", [1, 2])
-def test_bf16_state_follows_fp64_until_its_increments_round_away(p):
+def test_bf16_state_follows_fp64_until_its_increments_round_away():
     """BF16 deviation storage on the same transient.  Each LSRK stage changes
     the stored deviation by dt B res, a fixed fraction of a BF16 unit that
-    shrinks with dt: on N = 4 the increments exceed the unit and the BF16
-    state matches the FP64 discrete solution (error within 1 %), while on
-    N = 8 (p = 1) they are about a tenth of the unit, are rounded away, and
-    the state falls behind (measured: 4.0e-2 against FP64's 1.25e-2).  So the
-    BF16 form shows no order beyond N = 4 on this problem; a reduced-precision
+    shrinks with dt, i.e. with h / (p + 1)^2: at p = 1 on N = 4 the increments
+    exceed the unit and the BF16 state matches the FP64 discrete solution
+    (error within 1 %), while at p = 1 on N = 8 and at p = 2 on N = 4 they are
+    rounded away and the state falls behind (measured: 4.0e-2 against FP64's
+    1.25e-2, and 3.5e-2 against 1.98e-2).  So the BF16 form shows no order of
+    accuracy on this problem beyond its coarsest meshes; a reduced-precision
     state limits refinement studies, not the throughput runs."""
-    e = advection_error(4, p, "bf16")
-    e64 = advection_error(4, p, "fp64")
-    print("bf16 p=%d N=4" % p, e, "fp64", e64)
+    e = advection_error(4, 1, "bf16")
+    e64 = advection_error(4, 1, "fp64")
+    print("bf16 p=1 N=4", e, "fp64", e64)
     assert abs(e - e64) < 0.01 * e64, (e, e64)
-    if p == 1:
-        e8, e8_64 = advection_error(8, 1, "bf16"), advection_error(8, 1, "fp64")
-        print("bf16 p=1 N=8", e8, "fp64", e8_64)
-        assert e8 > 2 * e8_64            # the rounding-away of small increments, as stated
+    e8, e8_64 = advection_error(8, 1, "bf16"), advection_error(8, 1, "fp64")
+    print("bf16 p=1 N=8", e8, "fp64", e8_64)
+    assert e8 > 2 * e8_64            # the rounding-away of small increments, as stated
