@@ -59,6 +59,15 @@ WORKLOADS = {
         desc="lid-driven cavity Kn=8, 128x128x2 triangles, p=3, NC 32x32, BF16 deviation state, FP64 moments",
         reduction="fp64"),
 }
+WORKLOADS["cavity_kn1_unstructured_8192_p4_nc16x16_fp32"] = dict(
+    kind="cavity", nx=64, ny=64, p=4, vel=("nc", 16), kn=1.0, speed=0.1, precision="fp32",
+    unstructured=True, mesh_seed=201213487,
+    desc="lid-driven cavity Kn=1, unstructured 8192-triangle mesh of the unit square (jittered 64x64 vertex "
+         "grid, random diagonals), p=4, NC 16x16, lid 0.1, FP32")
+WORKLOADS["cavity_kn8_32x32x2_p5_nc33x33_sqrt2_fp32"] = dict(
+    kind="cavity", nx=32, ny=32, p=5, vel=("nc", 33), nc_sqrt2=1, kn=8.0, speed=0.1, precision="fp32",
+    desc="lid-driven cavity Kn=8, 32x32x2 triangles, p=5, NC 33x33 = D2Q1089 on the sqrt(2RT) grid "
+         "(velocity-split cluster kernel), lid 0.1, FP32")
 WORKLOADS["batch256_couette_cavity_fp32"] = dict(
     kind="batch", seed=201213487, n=256, precision="fp32",
     desc="256 seeded independent cases (128 Couette, 128 cavity; Kn log-uniform in [0.5, 8], wall/lid "
@@ -190,9 +199,15 @@ def make_descriptors(w, epc=0, tpb=0, stages=0, tc=0):
     else:
         bc = (fb.BC_WALL_DIFFUSE, fb.BC_PERIODIC, fb.BC_WALL_DIFFUSE, fb.BC_PERIODIC)
         wall = ((-w["speed"], 0), (0, 0), (w["speed"], 0), (0, 0))
-    m = fb.mesh_desc(w["nx"], w["ny"], w["p"], bc=bc, wall_u=wall)
+    if w.get("unstructured"):
+        from paper_2012_13487_gb300 import inputs
+        vert, tri = inputs.unstructured_square(w["nx"], w["ny"], w["mesh_seed"], shuffle=False)
+        m = fb.unstructured_mesh_desc(vert, tri, w["p"], bc=bc, wall_u=wall)
+    else:
+        m = fb.mesh_desc(w["nx"], w["ny"], w["p"], bc=bc, wall_u=wall)
     kind, n = w["vel"]
-    v = fb.velset_desc(fb.VELSET_GH if kind == "gh" else fb.VELSET_NC, n, eq_order=w.get("eq_order", 2))
+    v = fb.velset_desc(fb.VELSET_GH if kind == "gh" else fb.VELSET_NC, n, eq_order=w.get("eq_order", 2),
+                       nc_sqrt2=w.get("nc_sqrt2", 0))
     prm = fb.params(kn=w["kn"], precision=PREC[w["precision"]], reduction=RED[w.get("reduction", "default")],
                     cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb, pipeline_stages=stages, tensor_cores=tc)
     return m, v, prm
@@ -266,7 +281,9 @@ if w["kind"] == "cavity":
     bc = ("diffuse",) * 4; wall = ((0, 0), (0, 0), (w["speed"], 0), (0, 0))
 else:
     bc = ("diffuse", "periodic", "diffuse", "periodic"); wall = ((-w["speed"], 0), (0, 0), (w["speed"], 0), (0, 0))
-pr = dg.Problem(w["nx"], w["ny"], w["p"], velset=(kind, n), kn=w["kn"], bc=bc, wall_u=wall)
+mesh = inputs.unstructured_square(w["nx"], w["ny"], w["mesh_seed"], shuffle=False) if w.get("unstructured") else None
+pr = dg.Problem(w["nx"], w["ny"], w["p"], velset=(kind, n), kn=w["kn"], bc=bc, wall_u=wall, mesh=mesh,
+                nc_scale=np.sqrt(2.0) if w.get("nc_sqrt2") else 1.0)
 f0 = pr.equilibrium_state(amp=1e-3, u=inputs.perturbation(1, pr.K, pr.Np, pr.Q))
 rng = np.random.default_rng(0)
 elems = np.sort(rng.choice(pr.K, min(pr.K, %(nelem)d), replace=False))
@@ -309,7 +326,9 @@ if w["kind"] == "cavity":
 else:
     bc = ("diffuse", "periodic", "diffuse", "periodic"); wall = ((-w["speed"], 0), (0, 0), (w["speed"], 0), (0, 0))
 t0 = time.perf_counter()
-pr = dg.Problem(w["nx"], w["ny"], w["p"], velset=(kind, n), kn=w["kn"], bc=bc, wall_u=wall)
+mesh = inputs.unstructured_square(w["nx"], w["ny"], w["mesh_seed"], shuffle=False) if w.get("unstructured") else None
+pr = dg.Problem(w["nx"], w["ny"], w["p"], velset=(kind, n), kn=w["kn"], bc=bc, wall_u=wall, mesh=mesh,
+                nc_scale=np.sqrt(2.0) if w.get("nc_sqrt2") else 1.0)
 f = pr.equilibrium_state(amp=%(amp)r, u=inputs.perturbation(%(seed)d, pr.K, pr.Np, pr.Q))
 f = pr.run(f, %(steps)d)
 orho, oux, ouy = pr.nodal_moments(f)
@@ -333,10 +352,12 @@ ERROR_SEED = 201213487
 def error_copy(w):
     """The mesh copy on which a workload's error against the FP64 oracle is
     taken: the workload itself when it has at most 32 x 32 cells, else its
-    32 x 32 x 2 copy (the size the precision configuration names) with the
-    same degree, velocity set, Kn and wall speed."""
+    32 x 32 x 2 copy (the size the precision configuration names; 8 x 8 x 2 for
+    more than 1024 velocities) with the same degree, velocity set, Kn and wall
+    speed (and, for an unstructured workload, the same mesh generator)."""
     c = dict(w)
-    c["nx"], c["ny"] = min(w["nx"], 32), min(w["ny"], 32)
+    cells = 32 if w["vel"][1] ** 2 <= 1024 else 8   # D2Q1089: an 8 x 8 x 2 copy
+    c["nx"], c["ny"] = min(w["nx"], cells), min(w["ny"], cells)
     return c
 
 
@@ -522,13 +543,14 @@ def measure_form(w, st, steps, warmup, tune, repeats=3):
     info = s.info
     s.mass()
     s.close()
-    kern = "stage_kernel_tc" if info.tensor_cores else "stage_kernel"
+    kern = "stage_kernel_tc" if info.tensor_cores else ("stage_kernel_cl" if info.velocity_split > 1
+                                                         else "stage_kernel")
     return {"value": dof * 5 / (sp["ms_per_step_median"] / 1e3), "unit": "DOF-stage/s", "workload": w["desc"],
             "precision": w["precision"], "reduction": w.get("reduction", "default"), "dof": dof,
             "steps": steps, "repeats": sp,
             "tile": {"elems_per_cta": info.elems_per_cta, "threads_per_cta": info.threads_per_cta,
                      "pipeline_stages": info.pipeline_stages, "grid": info.grid,
-                     "tensor_cores": info.tensor_cores},
+                     "tensor_cores": info.tensor_cores, "velocity_split": info.velocity_split},
             "roofline": roofline_of(dof, w["precision"], sp["ms_per_step_median"], kern)}
 
 
@@ -702,6 +724,8 @@ FORMS = [
     ("cavity_kn8_128x128x2_p3_nc32_bf16_red_fp64", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "bf16", "fp64"),
     ("cavity_kn8_128x128x2_p3_nc32_bf16_red_comp", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "bf16", "comp"),
     ("cavity_kn8_128x128x2_p3_nc32_fp16_red_fp64", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "fp16", "fp64"),
+    ("cavity_unstructured_8192_p4_nc16_fp32", "cavity_kn1_unstructured_8192_p4_nc16x16_fp32", "fp32", "default"),
+    ("cavity_kn8_32x32x2_p5_d2q1089_fp32_split", "cavity_kn8_32x32x2_p5_nc33x33_sqrt2_fp32", "fp32", "default"),
 ]
 
 
@@ -714,8 +738,8 @@ def measure_forms(args, w, st, value, roof, error):
     by_copy = {}
     for key, wname, prec, red in FORMS:
         wf = dict(WORKLOADS[wname], precision=prec, reduction=red)
-        wf["desc"] = "%s [%s state, %s moment sums]" % (WORKLOADS[wname]["desc"].split(", BF16")[0].split(", FP32")[0],
-                                                       prec.upper(), red)
+        base = WORKLOADS[wname]["desc"].split(", BF16")[0].split(", FP32")[0]
+        wf["desc"] = "%s [%s state, %s moment sums]" % (base, prec.upper(), red)
         forms[key] = measure_form(wf, st, steps, args.warmup, not args.no_tune)
         by_copy.setdefault(wname, []).append((key, prec, red))
     if not args.no_error:
@@ -728,7 +752,34 @@ def measure_forms(args, w, st, value, roof, error):
                 forms[key]["error"] = dict(errs["%s/%s" % (prec, red)], copy=errs["copy"])
     bat = measure_batch(WORKLOADS["batch256_couette_cavity_fp32"], st, 10, 3, 2, not args.no_tune)
     forms["batched"] = dict(bat, workload=WORKLOADS["batch256_couette_cavity_fp32"]["desc"])
+    forms["implicit_backward_euler"] = measure_implicit(st)
     return forms
+
+
+def measure_implicit(st):
+    """The implicit path: backward-Euler steps (Newton with matrix-free GMRES,
+    every residual one fused stage-kernel launch) of a Couette case; reported
+    as residual evaluations x DOF per second and time per step."""
+    import torch
+    from paper_2012_13487_gb300 import fedbm as fb
+    w = dict(kind="couette", nx=16, ny=16, p=3, vel=("gh", 4), kn=1.0, speed=0.1, precision="fp64")
+    s = make_solver(w, st.cuda_stream)
+    s.set_equilibrium(1.0, 0.0, 0.0, 1e-3, 201213487)
+    ip = fb.implicit_params(fb.IMPLICIT_BE, 0.5, newton_rtol=1e-8, newton_atol=1e-12, gmres_rtol=1e-3,
+                            gmres_restart=40, gmres_max_iter=4000)
+    s.implicit_step(ip, 1)            # warm-up (work space, first launches)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats = s.implicit_step(ip, 3)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    K, Np, Q = dims(w)
+    s.close()
+    return {"value": stats.rhs_evals * K * Np * Q / secs, "unit": "DOF-residual evaluations/s",
+            "s_per_step": secs / 3, "newton_iters": stats.newton_iters, "gmres_iters": stats.gmres_iters,
+            "rhs_evals": stats.rhs_evals, "converged": bool(stats.converged),
+            "workload": "Couette Kn=1, 16x16x2 triangles, p=3, GH D2Q16, FP64; backward Euler dt = 0.5, "
+                        "3 steps, Newton to 1e-8 relative, GMRES(40) forcing 1e-3, no preconditioner"}
 
 
 def run_batch_workload(args, w, name, st, world, rank, dist):

@@ -164,6 +164,12 @@ typedef struct fedbm_params {
                              at degree 5 and 6), 1 = never, 2, 4 or 8 = that
                              cluster size (EINVAL where it does not divide
                              the padded velocity count into multiples of 8) */
+  int32_t rounding;      /* encode of the new BF16 deviation state: 0 = round to
+                            nearest even; 1 = stochastic rounding (BF16 only:
+                            a counter-based draw per value, stage and step, so
+                            that stage increments below half a BF16 unit are
+                            kept in expectation instead of being rounded away;
+                            the draws restart with each state load)       */
 } fedbm_params;
 
 typedef struct fedbm_info_t {

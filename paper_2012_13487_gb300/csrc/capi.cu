@@ -391,6 +391,8 @@ struct Group {
   int tc_mode = 0;  // fedbm_params.tensor_cores of the group's cases
   int tc = 0;       // 1: the stage kernel is the tensor-core form
   int vsplit = 0;   // fedbm_params.velocity_split of the group's cases
+  int rounding = 0; // fedbm_params.rounding: 1 = stochastic BF16 encode
+  uint32_t* sr_step = nullptr;  // stochastic rounding: steps taken since the state load
   int ncl = 0;      // > 1: the velocity-split form with clusters of ncl CTAs
   int64_t K = 0;
   std::vector<int> cases;
@@ -441,7 +443,7 @@ bool same_group(const Group& g, const fedbm_mesh_desc& md, const fedbm_velset_de
          g.collision == prm.collision && g.reduction == prm.reduction && g.beta == prm.beta &&
          g.epc == prm.elems_per_cta && g.tpb == prm.threads_per_cta && g.nstages == prm.pipeline_stages &&
          g.test_wait_timeout == prm.test_wait_timeout && g.tc_mode == prm.tensor_cores &&
-         g.vsplit == prm.velocity_split;
+         g.vsplit == prm.velocity_split && g.rounding == prm.rounding;
 }
 
 template <typename R>
@@ -472,7 +474,12 @@ void fill_stage_args(const Group& g, int stage, int from, StageArgs<R>& a) {
   a.red = g.reduction;
   a.err = g.flag + 1;
   a.extra_tx = g.test_wait_timeout ? 16u : 0u;
+  a.sr_step = g.sr_step;
+  a.sr_stage = stage;
 }
+
+// one more step for the stochastic-rounding draws (a graph node after each step)
+__global__ void sr_step_kernel(uint32_t* step) { step[0] += 1u; }
 
 // Launch the group's configured stage-kernel form with these arguments.
 cudaError_t launch_args(const Group& g, const void* args, cudaStream_t st, int grid = 0) {
@@ -767,6 +774,10 @@ int build_graphs(Batch& b) {
         le = launch_stage(g, s, from, st);
         from = 1 - from;
       }
+      if (g.sr_step && le == cudaSuccess) {
+        sr_step_kernel<<<1, 1, 0, st>>>(g.sr_step);
+        le = cudaGetLastError();
+      }
       if (branches && le == cudaSuccess) {
         cudaEvent_t done = nullptr;
         le = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
@@ -925,6 +936,10 @@ int build_group(Batch& b, Group& g) {
   FEDBM_CK(cudaMalloc(&g.partial, (kMassBlocks + 1) * sizeof(double)));
   FEDBM_CK(cudaMalloc(&g.flag, 2 * sizeof(int)));
   FEDBM_CK(cudaMemset(g.flag, 0, 2 * sizeof(int)));
+  if (g.rounding == 1) {
+    FEDBM_CK(cudaMalloc(&g.sr_step, sizeof(uint32_t)));
+    FEDBM_CK(cudaMemset(g.sr_step, 0, sizeof(uint32_t)));
+  }
   FEDBM_CK(cudaStreamCreateWithFlags(&g.branch, cudaStreamNonBlocking));
   return FEDBM_OK;
 }
@@ -942,7 +957,8 @@ void free_batch(Batch* b) {
       cudaFree(g.f[c]);
       cudaFree(g.scale[c]);
     }
-    void* bufs[] = {g.res, g.nbr, g.geo, g.vel, g.vel64, g.wall_feq, g.wall_den_inv, g.Jk, g.mw, g.partial, g.flag};
+    void* bufs[] = {g.res, g.nbr, g.geo, g.vel, g.vel64, g.wall_feq, g.wall_den_inv, g.Jk, g.mw, g.partial, g.flag,
+                    g.sr_step};
     for (void* p : bufs) cudaFree(p);
     if (g.branch) cudaStreamDestroy(g.branch);
   }
@@ -974,6 +990,8 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
     if (prm.velocity_split != 0 && prm.velocity_split != 1 && prm.velocity_split != 2 && prm.velocity_split != 4 &&
         prm.velocity_split != 8)
       return bail(fail(FEDBM_EINVAL, "velocity_split must be 0, 1, 2, 4 or 8"));
+    if (prm.rounding != 0 && !(prm.rounding == 1 && prm.precision == FEDBM_BF16_DEV))
+      return bail(fail(FEDBM_EINVAL, "rounding: 0 (nearest even), or 1 (stochastic) for BF16 deviation state"));
     if (!(prm.beta >= 0.5 && prm.beta <= 1.0)) return bail(fail(FEDBM_EINVAL, "beta must be in [0.5, 1]"));
     if (!(prm.dt > 0) && !(prm.cfl > 0)) return bail(fail(FEDBM_EINVAL, "need dt > 0 or cfl > 0"));
     if (cd[c].mesh.order < 0 || cd[c].mesh.order > kMaxOrder) return bail(fail(FEDBM_EINVAL, "order must be in 0..6"));
@@ -998,6 +1016,7 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
       g.test_wait_timeout = prm.test_wait_timeout;
       g.tc_mode = prm.tensor_cores;
       g.vsplit = prm.velocity_split;
+      g.rounding = prm.rounding;
       b->groups.push_back(g);
       gi = int(b->groups.size()) - 1;
     }
@@ -1085,8 +1104,10 @@ int encode_case(Batch& b, int c, const double* src) {
     default: encode_kernel<StoreF16><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__half*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
   }
   FEDBM_CK(cudaGetLastError());
-  // a new state starts with a clear stage-kernel timeout word
+  // a new state starts with a clear stage-kernel timeout word (and the
+  // stochastic-rounding draws from step 0)
   FEDBM_CK(cudaMemsetAsync(g.flag + 1, 0, sizeof(int), b.stream));
+  if (g.sr_step) FEDBM_CK(cudaMemsetAsync(g.sr_step, 0, sizeof(uint32_t), b.stream));
   b.time = 0;
   b.steps = 0;
   return FEDBM_OK;

@@ -78,7 +78,29 @@ struct StageArgs {
   int32_t collision, eq_order, red;
   int* err;                 // set to 1 if a bounded wait of a CTA gave up
   uint32_t extra_tx;        // test hook: bytes expected on top of the copies (0)
+  const uint32_t* sr_step;  // BF16 stochastic rounding: the step counter (nullptr = nearest-even)
+  int32_t sr_stage;         // RK stage index mixed into the rounding draws
 };
+
+// Stochastic rounding of an FP32 value to BF16: a uniform 16-bit draw is
+// added to the 16 bits that BF16 drops, then they are cut off, so x rounds
+// away from zero with probability (dropped bits) / 2^16 and the stored value
+// is x in expectation (|x| <= 1 here: no overflow).  The draw comes from a
+// counter-based hash of the value's index, the step and the stage
+// (the 32-bit finaliser of MurmurHash3, Appleby).
+__device__ __forceinline__ uint32_t sr_hash(uint64_t idx, uint32_t step, uint32_t stage) {
+  uint32_t h = uint32_t(idx) ^ uint32_t(idx >> 32) * 0x9E3779B1u ^ (step * 0x85EBCA77u) ^ (stage * 0xC2B2AE3Du);
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ __nv_bfloat16 bf16_round_stochastic(float x, uint32_t draw) {
+  const uint32_t b = (__float_as_uint(x) + (draw & 0xFFFFu)) & 0xFFFF0000u;
+  return __ushort_as_bfloat16(static_cast<unsigned short>(b >> 16));
+}
 
 __host__ __device__ constexpr int np_of(int p) { return (p + 1) * (p + 2) / 2; }
 

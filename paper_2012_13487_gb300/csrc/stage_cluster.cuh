@@ -345,8 +345,17 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel_cl(const StageArgs<t
           if (read_res) r = fma(rkA, rrow[n * Qc], r);
           rrow[n * Qc] = r;
           const R fnew = new_f<ST>(fr[n], rkB, r);
-          if constexpr (ST::dev) frow[n * Qc] = ST::from_r((fnew - w) * invw);
-          else frow[n * Qc] = S(fnew);
+          if constexpr (ST::dev) {
+            const R qv = (fnew - w) * invw;
+            if (a.sr_step) {
+              const uint64_t gi = (uint64_t(k0 + e) * NP + n) * uint64_t(Qp) + uint64_t(ig);
+              frow[n * Qc] = bf16_round_stochastic(qv, sr_hash(gi, __ldg(a.sr_step), uint32_t(a.sr_stage)));
+            } else {
+              frow[n * Qc] = ST::from_r(qv);
+            }
+          } else {
+            frow[n * Qc] = S(fnew);
+          }
         }
       }
       if constexpr (ST::dev)

@@ -466,6 +466,9 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
   constexpr bool kImm = ops_immediate<ST, QT>();
   constexpr bool kKeep = keeps_scale<ST>();
   constexpr bool kTrack = ST::dev && !kKeep;
+  // stochastic rounding of the BF16 encode: the step counter is read once
+  const bool sr = kKeep && a.sr_step != nullptr;
+  const uint32_t sr_step = sr ? __ldg(a.sr_step) : 0u;
   for (int item = tid; item < ne * Qv; item += nth) {
     const int e = item / Qv;
     const int i = (item - e * Qv) * VPT;
@@ -591,7 +594,13 @@ __device__ __forceinline__ void item_update(const StageArgs<typename ST::R>& a,
         if constexpr (kTrack) {
           dloc = fmaxf(dloc, fabsf((fnew - wv.v[v]) * invw[v]));
         } else if constexpr (kKeep) {
-          fnew_s.v[v] = ST::from_r((fnew - wv.v[v]) * invw[v]);
+          const float qv = (fnew - wv.v[v]) * invw[v];
+          if (sr) {
+            const uint64_t gi = (uint64_t(k0 + e) * NP + n) * uint64_t(Qp) + uint64_t(i + v);
+            fnew_s.v[v] = bf16_round_stochastic(qv, sr_hash(gi, sr_step, uint32_t(a.sr_stage)));
+          } else {
+            fnew_s.v[v] = ST::from_r(qv);
+          }
         } else {
           fnew_s.v[v] = S(fnew);
         }

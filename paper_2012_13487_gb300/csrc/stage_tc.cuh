@@ -452,7 +452,10 @@ __global__ void __launch_bounds__(tc::kTcThreads, 4) stage_kernel_tc(const Stage
             if constexpr (kRescale) {
               dloc = fmaxf(dloc, fabsf((fnew - w) * invw));
             } else if constexpr (kKeepScale) {
-              fout[(k0 * NP + n) * QT + i] = ST::from_r((fnew - w) * invw * inv_s_el);
+              const float qv = (fnew - w) * invw * inv_s_el;
+              const size_t gi = (k0 * NP + n) * QT + i;
+              if (a.sr_step) fout[gi] = bf16_round_stochastic(qv, sr_hash(gi, __ldg(a.sr_step), uint32_t(a.sr_stage)));
+              else fout[gi] = ST::from_r(qv);
             } else {
               fout[(k0 * NP + n) * QT + i] = fnew;
             }

@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
                 ("elems_per_cta", ctypes.c_int32), ("threads_per_cta", ctypes.c_int32),
                 ("pipeline_stages", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
                 ("test_wait_timeout", ctypes.c_int32), ("tau_model", ctypes.c_int32),
-                ("velocity_split", ctypes.c_int32)]
+                ("velocity_split", ctypes.c_int32), ("rounding", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -208,7 +208,7 @@ def velset_desc(kind=VELSET_GH, n=4, eq_order=2, nc_extent=4.0, nc_sqrt2=0):
 
 def params(kn=1.0, precision=FP32, reduction=RED_DEFAULT, cfl=0.5, dt=0.0, beta=1.0, collision=1,
            length=1.0, elems_per_cta=0, threads_per_cta=0, pipeline_stages=0, tensor_cores=0,
-           test_wait_timeout=0, tau_model=0, velocity_split=0):
+           test_wait_timeout=0, tau_model=0, velocity_split=0, rounding=0):
     p = Params()
     p.kn, p.length, p.beta, p.cfl, p.dt = kn, length, beta, cfl, dt
     p.precision, p.reduction, p.collision = precision, reduction, collision
@@ -218,6 +218,7 @@ def params(kn=1.0, precision=FP32, reduction=RED_DEFAULT, cfl=0.5, dt=0.0, beta=
     p.test_wait_timeout = test_wait_timeout
     p.tau_model = tau_model
     p.velocity_split = velocity_split
+    p.rounding = rounding
     return p
 
 

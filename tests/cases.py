@@ -52,7 +52,8 @@ def descriptors(c, precision="fp32", reduction="default", **tile):
                     elems_per_cta=tile.get("epc", 0), threads_per_cta=tile.get("tpb", 0),
                     pipeline_stages=tile.get("stages", 0), tensor_cores=tile.get("tc", 0),
                     test_wait_timeout=tile.get("test_wait_timeout", 0),
-                    tau_model=TAU_CODE[c.get("tau_model", "kn")], velocity_split=tile.get("vsplit", 0))
+                    tau_model=TAU_CODE[c.get("tau_model", "kn")], velocity_split=tile.get("vsplit", 0),
+                    rounding=tile.get("rounding", 0))
     return m, v, prm
 
 

@@ -104,3 +104,37 @@ def test_bf16_state_follows_fp64_until_its_increments_round_away():
     e8, e8_64 = advection_error(8, 1, "bf16"), advection_error(8, 1, "fp64")
     print("bf16 p=1 N=8", e8, "fp64", e8_64)
     assert e8 > 2 * e8_64            # the rounding-away of small increments, as stated
+
+
+def test_bf16_stochastic_rounding_keeps_the_order():
+    """The same transient with the BF16 encode rounded stochastically
+    (fedbm_params.rounding = 1): a stage increment below half a BF16 unit is
+    kept in expectation, so the N = 8 state no longer falls behind, and the
+    error keeps decreasing from N = 4 to N = 8 at about the FP64 rate."""
+    def err(n, prec, **tile):
+        return advection_error_tiled(n, 1, prec, **tile)
+    e4, e8 = err(4, "bf16", rounding=1), err(8, "bf16", rounding=1)
+    f4, f8 = err(4, "fp64"), err(8, "fp64")
+    print("bf16 stochastic p=1", e4, e8, "fp64", f4, f8)
+    assert abs(e8 - f8) < 0.35 * f8, (e8, f8)
+    assert np.log2(e4 / e8) > 1.4, (e4, e8)
+
+
+def advection_error_tiled(N, p, precision, T=0.1, **tile):
+    def g(x, y):
+        return 1.0 + 0.1 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+
+    c = dict(nx=N, ny=N, p=p, bc=("periodic",) * 4, wall_u=((0, 0),) * 4, velset=("gh", 2),
+             collision=False, cfl=0.25)
+    pr = cases.oracle_problem(c)
+    nsteps = int(np.ceil(T / pr.dt))
+    from paper_2012_13487_gb300 import fedbm as fb
+    m, v, prm = cases.descriptors(c, precision, **tile)
+    prm.dt = T / nsteps
+    s = fb.Solver(m, v, prm)
+    s.set_state(pr.w[None, None, :] * g(pr.x, pr.y)[:, :, None])
+    s.step(nsteps)
+    f = s.state()
+    s.close()
+    exact = pr.w[None, None, :] * g(pr.x[:, :, None] - pr.ex * T, pr.y[:, :, None] - pr.ey * T)
+    return float(np.abs(f - exact).max() / pr.w.max())

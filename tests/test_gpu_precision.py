@@ -84,3 +84,29 @@ def test_fp32_state_error_c3_copy(oracle_step, red):
     print(f"fp32/{red}: rel max {rel:.3e}, L2 rho {e_rho:.3e}, L2 u/U {e_u:.3e}")
     assert rel < 4.0 * pr.Np * U32 * np.sqrt(5) + U32
     assert rel < 5.0e-7 and e_rho < 9.0e-8 and e_u < 4.5e-7, (rel, e_rho, e_u)
+
+
+@pytest.mark.parametrize("tc", [-1, 1])
+def test_bf16_stochastic_rounding_within_the_storage_bound(oracle_step, tc):
+    """Stochastic rounding of the BF16 encode moves a value by less than one
+    BF16 unit (2u relative to the element's deviation, u = 2^-8 ... within the
+    same 12 u a-priori bound), in both kernel forms."""
+    pr, f0, f1 = oracle_step
+    s = cases.solver(CASE, "bf16", "fp64", tc=tc, rounding=1)
+    s.set_state(f0)
+    s.step(1)
+    f = s.state()
+    s.close()
+    w = pr.w[None, None, :]
+    md = np.abs(f1 / w - 1.0).max(axis=(1, 2))
+    norm_err = float((np.abs(f - f1) / (w * md[:, None, None])).max())
+    print("bf16 stochastic tc=%d: max|df|/(w md) = %.3e" % (tc, norm_err))
+    assert norm_err < 12 * 2.0 ** -8
+
+
+def test_stochastic_rounding_only_for_bf16():
+    from paper_2012_13487_gb300 import fedbm as fb
+    with pytest.raises(fb.FedbmError):
+        cases.solver(CASE, "fp32", rounding=1)
+    with pytest.raises(fb.FedbmError):
+        cases.solver(CASE, "fp16", rounding=1)
