@@ -570,14 +570,23 @@ int configure_cluster(Batch& b, Group& g, int ncl) {
   return FEDBM_OK;
 }
 
-// Smallest cluster size whose velocity slice fits shared memory, 0 if none.
+// Cluster size of the automatic velocity-split form: the one that keeps the
+// most CTAs resident on the device (smaller slices let more CTAs share an SM),
+// the smaller one on a tie; 0 if no slice fits shared memory.
 int auto_cluster(const Group& g) {
   const StageEntry e = stage_entry(g.p);
+  int best = 0, best_ctas = 0;
   for (int ncl : {2, 4, 8}) {
     const size_t smem = e.cl_smem(g.store, g.Qp, ncl, 1);
-    if (smem > 0 && smem <= 227 * 1024) return ncl;
+    if (smem == 0 || smem > 227 * 1024) continue;
+    if (e.set_smem_cl(g.store, smem) != cudaSuccess) continue;
+    const int ctas = e.occupancy_cl(g.store, ncl, smem) * ncl;
+    if (ctas > best_ctas) {
+      best = ncl;
+      best_ctas = ctas;
+    }
   }
-  return 0;
+  return best;
 }
 
 // Tile shape, pipeline depth and persistent grid of a group's stage kernel.

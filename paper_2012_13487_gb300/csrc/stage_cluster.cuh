@@ -88,8 +88,16 @@ __host__ __device__ inline Layout layout(int epc, int Qc, int s_bytes, int r_byt
   return o;
 }
 
+// Two resident CTAs of 256 threads per SM (at most 128 registers) for the
+// FP32-arithmetic forms: one CTA per SM leaves too few warps to hide latency;
+// the FP64 form keeps the whole register file (it would spill heavily).
 template <class ST>
-__global__ void __launch_bounds__(kThreads, 1) stage_kernel_cl(const StageArgs<typename ST::R> a) {
+__host__ __device__ constexpr int cl_min_blocks() {
+  return sizeof(typename ST::R) == 8 ? 1 : 2;
+}
+
+template <class ST>
+__global__ void __launch_bounds__(kThreads, cl_min_blocks<ST>()) stage_kernel_cl(const StageArgs<typename ST::R> a) {
   using R = typename ST::R;
   using S = typename ST::S;
   extern __shared__ __align__(128) unsigned char smem[];

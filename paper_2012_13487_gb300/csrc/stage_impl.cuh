@@ -13,15 +13,17 @@
 // the old one).
 //
 // Phases of a CTA:
-//   1. bulk-copy (TMA) the element tile f[k0:k0+epc][Np][Qp], the residual
-//      tile and every neighbour face row into shared memory;
+//   1. bulk-copy (TMA) the element tile f[k0:k0+epc][Np][Qp] and its geometry
+//      (first barrier), the residual tile and every neighbour face row (second
+//      barrier) into shared memory;
 //   2. node moments rho, u (Sec. II.A.2) by a G-lane reduction per node, kept
-//      as the coefficients of f^eq/tau per node;
+//      as the coefficients of f^eq/tau per node, while the second part lands;
 //   3. wall numerators sum_{e.n>0} (e.n) f^- of eq. FullBC per wall node;
 //   4. residual and update, one thread per (element, velocity) item, with
-//      Dr, Ds, LIFT as constant-memory operands of unrolled FMAs (the 16-bit
-//      forms up to degree 4 take two velocities per thread as packed FP32
-//      pairs, fma.rn.f32x2);
+//      Dr, Ds, LIFT as instruction immediates (compile-time tables) or
+//      constant-memory operands of unrolled FMAs (the 16-bit forms up to
+//      degree 3 take two velocities per thread as packed FP32 pairs,
+//      fma.rn.f32x2);
 //   5. deviation forms only: per-element scale from max |f/w - 1|, encode;
 //   6. bulk-store the new state and residual tiles.
 #include "device_common.cuh"
@@ -659,17 +661,23 @@ __device__ void issue_tile_loads(const StageArgs<typename ST::R>& a, StageSmem<t
       sm.dmax[v] = 0u;
     }
   }
+  // two barriers: bar[0] for the element tile and geometry (needed first, by
+  // the moment and wall-numerator reductions), bar[1] for the residual tile
+  // and the neighbour traces (needed only by the update), so the reductions
+  // start while the larger second part is still in flight
+  uint64_t* bar_rt = sm.bar + 1;
   uint32_t bytes = 0;
-  if (lane == 0) bytes += tile_bytes + geo_bytes + (read_res ? res_bytes : 0u) + a.extra_tx;
+  if (lane == 0) bytes += (read_res ? res_bytes : 0u);
   for (int row = lane; row < ne * NF; row += 32) {
     const int code = __ldg(a.nbr + (k0 + row / NF) * 3 + (row % NF) / NFP);
     if (code >= 0) bytes += uint32_t(row_bytes);
   }
-  mbar_arrive_expect_tx(sm.bar, bytes);
+  mbar_arrive_expect_tx(sm.bar, lane == 0 ? tile_bytes + geo_bytes + a.extra_tx : 0u);
+  mbar_arrive_expect_tx(bar_rt, bytes);
   if (lane == 0) {
     bulk_load(sm.f, fin + k0 * NP * Qp, tile_bytes, sm.bar);
     bulk_load(sm.geo, a.geo + k0 * kGeoStrideDev, geo_bytes, sm.bar);
-    if (read_res) bulk_load(sm.res, a.res + k0 * NP * Qp, res_bytes, sm.bar);
+    if (read_res) bulk_load(sm.res, a.res + k0 * NP * Qp, res_bytes, bar_rt);
   }
   for (int row = lane; row < ne * NF; row += 32) {
     const int e = row / NF, fc = (row % NF) / NFP, aa = row % NFP;
@@ -680,7 +688,7 @@ __device__ void issue_tile_loads(const StageArgs<typename ST::R>& a, StageSmem<t
       const int a2 = (code & 1) ? NFP - 1 - aa : aa;
       const int rs = a2 * (P + 1) - a2 * (a2 - 1) / 2;
       const int node = fn == 0 ? a2 : (fn == 1 ? rs + (P - a2) : rs);
-      bulk_load(sm.tr + size_t(row) * Qp, fin + (kn * NP + node) * Qp, uint32_t(row_bytes), sm.bar);
+      bulk_load(sm.tr + size_t(row) * Qp, fin + (kn * NP + node) * Qp, uint32_t(row_bytes), bar_rt);
     }
   }
 }
@@ -712,7 +720,11 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
   }
   if (tid == 0) {
     mbar_init(stage(0).bar, 32);
-    if (two) mbar_init(stage(1).bar, 32);  // the second stage exists only when nstages == 2
+    mbar_init(stage(0).bar + 1, 32);
+    if (two) {  // the second stage exists only when nstages == 2
+      mbar_init(stage(1).bar, 32);
+      mbar_init(stage(1).bar + 1, 32);
+    }
     fence_mbar_init();
     fence_proxy_async_smem();
   }
@@ -751,8 +763,11 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
     if (__syncthreads_or(!ok)) {
       if (tid == 0 && a.err) atomicExch(a.err, 1);
       // let copies still in flight land before the CTA exits
-      if (tid < 32 && two && next < ntiles)
+      if (tid < 32) mbar_wait_bounded(sm.bar + 1, parity, 1000000000ull);
+      if (tid < 32 && two && next < ntiles) {
         mbar_wait_bounded(stage((j + 1) & 1).bar, uint32_t(((j + 1) >> 1) & 1), 1000000000ull);
+        mbar_wait_bounded(stage((j + 1) & 1).bar + 1, uint32_t(((j + 1) >> 1) & 1), 1000000000ull);
+      }
       if (tid == 0) bulk_wait_read();
       return;
     }
@@ -786,7 +801,17 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
     }
     // ---- 3. wall numerators ------------------------------------------------------
     if (a.wall_any) tile_wall_numerators<ST, QT>(a, sm.f, sm.geo, sm.nbr, sm.scale, sm.wn, ne, sm.vel);
-    __syncthreads();
+    // the residual tile and the neighbour traces (bar[1]), as for bar[0]
+    ok = true;
+    if (tid < 32) ok = mbar_wait_bounded(sm.bar + 1, parity, 2000000000ull);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && a.err) atomicExch(a.err, 1);
+      if (tid < 32 && two && next < ntiles)
+        mbar_wait_bounded(stage((j + 1) & 1).bar + 1, uint32_t(((j + 1) >> 1) & 1), 1000000000ull);
+      if (tid == 0) bulk_wait_read();
+      return;
+    }
+    if (tid >= 32) mbar_try_wait(sm.bar + 1, parity);
 
     // ---- 4. residual and update ----------------------------------------------------
     float dmax = 0.f;  // deviation forms: running max |f/w - 1| of element emax
