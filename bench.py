@@ -840,10 +840,13 @@ def main():
                     "the p=5 Couette and Kn=8 cavity configurations, the batch)")
     ap.add_argument("--no-error", action="store_true", help="skip the error against the oracle")
     ap.add_argument("--repeats", type=int, default=REPEATS, help="timed regions of --steps steps (median reported)")
+    ap.add_argument("--reduction", default=None, choices=sorted(RED), help="moment sums (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     w = WORKLOADS[args.workload]
+    if args.reduction:
+        w = dict(w, reduction=args.reduction)
     if args.impl == "reference":
         run_reference(args, w, args.workload)
     else:

@@ -76,3 +76,37 @@ def test_full_size_cavity_gh16_three_steps(tc):
     tol = 4.0 * pr.Np * 2.0 ** -24 * np.sqrt(15) + 2.0 ** -24
     assert err <= tol, (err, tol)
     s.close()
+
+
+def test_full_batch256_sampled_cases_against_the_oracle():
+    """The seeded 256-case batch itself against the FP64 oracle: after one
+    LSRK step of the whole batch from each case's seeded perturbed rest state,
+    sampled cases (both kinds, both velocity sets, several degrees) are compared
+    with the oracle's step on sampled elements, within the FP32 rounding bound
+    of the parity tests."""
+    from paper_2012_13487_gb300 import inputs
+    w = bench.WORKLOADS["batch256_couette_cavity_fp32"]
+    cs = bench.batch_case_list(w)
+    b = bench.make_batch(cs, 0)
+    for i in range(len(cs)):
+        b.set_equilibrium(i, 1.0, 0.0, 0.0, 1e-3, 201213487 + i)
+    picks = [0, 37, 127, 128, 190, 255]
+    got = {}
+    b.step(1)
+    for i in picks:
+        got[i] = b.state(i)
+    b.close()
+    rng = np.random.default_rng(4)
+    for i in picks:
+        c = cs[i]
+        kind, n = c["vel"]
+        bc = ("diffuse",) * 4 if c["kind"] == "cavity" else ("diffuse", "periodic", "diffuse", "periodic")
+        wall = ((0, 0), (0, 0), (c["speed"], 0), (0, 0)) if c["kind"] == "cavity" else \
+            ((-c["speed"], 0), (0, 0), (c["speed"], 0), (0, 0))
+        pr = dg.Problem(c["nx"], c["ny"], c["p"], velset=(kind, n), kn=c["kn"], bc=bc, wall_u=wall)
+        f0 = pr.equilibrium_state(amp=1e-3, u=inputs.perturbation(201213487 + i, pr.K, pr.Np, pr.Q))
+        f1 = pr.run(f0, 1)
+        elems = np.sort(rng.choice(pr.K, min(pr.K, 64), replace=False))
+        err = np.abs(got[i][elems] - f1[elems]).max() / np.abs(f1).max()
+        tol = 4.0 * pr.Np * 2.0 ** -24 * np.sqrt(5) + 2.0 ** -24
+        assert err < tol, (i, c, err, tol)
