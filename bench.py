@@ -313,6 +313,31 @@ def oracle_sample(w, seconds, nelem=512, min_stages=1, max_stages=10 ** 9):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def oracle_sample_all_cores(w, seconds, nelem=512):
+    """The same oracle sample run by one single-threaded process per host core
+    at once (each on its own element sample): the aggregate DOF-stage/s of all
+    cores, as a CPU baseline that uses the whole host."""
+    ncores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    procs = []
+    for c in range(ncores):
+        script = ORACLE_SAMPLE_SCRIPT % dict(root=ROOT, w=json.dumps(w), seconds=seconds, nelem=nelem,
+                                             min_stages=1, max_stages=10 ** 9)
+        script = script.replace("default_rng(0)", "default_rng(%d)" % c)
+        procs.append(subprocess.Popen([sys.executable, "-c", script], stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True, env=env))
+    outs = []
+    for pr in procs:
+        o, e = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + e[-2000:])
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    secs = max(o["seconds"] for o in outs)
+    return {"dof_stages": sum(o["dof_stages"] for o in outs), "seconds": secs, "cores": ncores,
+            "elements": outs[0]["elements"], "K": outs[0]["K"]}
+
+
 ORACLE_ERROR_SCRIPT = r"""
 import json, sys, time
 sys.path.insert(0, %(root)r)
@@ -675,6 +700,11 @@ def run_ours(args, w, name):
                          "%d-element mesh, single thread, %.1f s" % (out["stages"], out["elements"],
                                                                      out["dof_stages"] // out["stages"],
                                                                      out["K"], out["seconds"])}
+        allc = oracle_sample_all_cores(w, seconds=min(args.cpu_seconds, 10.0))
+        cpu["all_cores"] = {"value": allc["dof_stages"] / allc["seconds"], "unit": "DOF-stage/s",
+                            "cores": allc["cores"], "kind": "oracle",
+                            "sample": "the same sample, one single-threaded oracle process per host core at "
+                                      "once, each on %d sampled elements of its own" % allc["elements"]}
     if rank == 0 and world == 1 and not args.no_error:
         with tempfile.TemporaryDirectory() as td:
             copy, paths = gpu_error_moments(w, [(w["precision"], w.get("reduction", "default"))], st, td)

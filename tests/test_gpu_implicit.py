@@ -108,3 +108,25 @@ def test_implicit_errors():
     with pytest.raises(fb.FedbmError) as e:
         s.implicit_step(fb.implicit_params(fb.IMPLICIT_CUSTOM, 0.1, A=[[0.5, 0.1], [0.2, 0.5]], b=[0.5, 0.5]), 1)
     assert e.value.code == fb.FEDBM_EINVAL
+
+
+@pytest.mark.parametrize("form", ["unstructured", "split"])
+def test_backward_euler_on_other_meshes_and_forms(form):
+    """The implicit path runs R through whatever stage kernel the solver has:
+    an unstructured mesh, or the velocity-split cluster form."""
+    if form == "unstructured":
+        c = cases.unstructured(cases.cavity(0, 0, 2, velset=("gh", 3), kn=1.0), 3, 2, seed=61)
+        tile = {}
+    else:
+        c = cases.couette(1, 2, 2, velset=("nc", 8), kn=1.0)
+        tile = {"vsplit": 2}
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=2e-2, seed=15)
+    dt = 10 * pr.dt
+    s = cases.solver(c, "fp64", **tile)
+    if form == "split":
+        assert s.info.velocity_split == 2
+    s.set_state(f0)
+    s.implicit_step(_tight(0, dt), 1)
+    f_or, _ = implicit.sdirk_step(pr, f0, dt, "be")
+    assert cases.rel_max_err(s.state(), f_or) < 1e-10

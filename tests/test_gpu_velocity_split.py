@@ -105,3 +105,10 @@ def test_split_rejections():
         cases.solver(c, "fp32", vsplit=8)
     with pytest.raises(fb.FedbmError):
         cases.solver(cases.cavity(2, 2, 2, velset=("nc", 16)), "fp16", vsplit=2)
+
+
+def test_split_on_an_unstructured_mesh():
+    c = cases.unstructured(cases.cavity(0, 0, 3, velset=("nc", 16), kn=2.0), 4, 3, seed=51)
+    pr, s, f0, f = _run(c, 3, "fp64", vsplit=4)
+    assert s.info.velocity_split == 4
+    assert cases.rel_max_err(f, pr.run(f0, 3)) < 1e-12
