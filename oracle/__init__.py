@@ -14,8 +14,9 @@ Knudsen number flows" (arXiv 2012.13487):
 
 * ``velset``  -- Gauss-Hermite and Newton-Cotes velocity sets (Sec. II.A.3,
   Table 1).
-* ``mesh``    -- structured split-square triangulation and its face
-  connectivity (Sec. II.B.1, Sec. III.A).
+* ``mesh``    -- structured split-square triangulation, unstructured
+  triangulations given as vertex / triangle lists, and their face
+  connectivity (Sec. II.B.1, Sec. III).
 * ``ops``     -- nodal DG operators on the reference triangle
   (Sec. II.B.1, eq. byparts), built from a Legendre-product basis and
   collapsed-coordinate quadrature.
@@ -24,6 +25,9 @@ Knudsen number flows" (arXiv 2012.13487):
   eq. byparts, LSRK(5,4) time marching, diagnostics.
 * ``couette`` -- the linearized Couette closed form (eq. exact, repaired)
   and a discrete-velocity steady solve that checks it.
+* ``implicit`` -- SDIRK time marching (backward Euler and two fourth-order
+  tableaux, Sec. II.B.3) with Newton's method on a dense finite-difference
+  Jacobian.
 
 Parity status of each function is stated in its docstring; the cavity
 workload has no printed solution, so beyond the method invariants its
