@@ -209,7 +209,8 @@ def make_descriptors(w, epc=0, tpb=0, stages=0, tc=0):
     v = fb.velset_desc(fb.VELSET_GH if kind == "gh" else fb.VELSET_NC, n, eq_order=w.get("eq_order", 2),
                        nc_sqrt2=w.get("nc_sqrt2", 0))
     prm = fb.params(kn=w["kn"], precision=PREC[w["precision"]], reduction=RED[w.get("reduction", "default")],
-                    cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb, pipeline_stages=stages, tensor_cores=tc)
+                    cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb, pipeline_stages=stages, tensor_cores=tc,
+                    rounding=w.get("rounding", 0))
     return m, v, prm
 
 
@@ -393,17 +394,20 @@ def gpu_error_moments(w, forms, st, tmpdir):
     import torch
     c = error_copy(w)
     paths = {}
-    for prec, red in forms:
-        wc = dict(c, precision=prec, reduction=red)
+    for form in forms:
+        prec, red = form[0], form[1]
+        rounding = form[2] if len(form) > 2 else 0
+        wc = dict(c, precision=prec, reduction=red, rounding=rounding)
         s = make_solver(wc, st.cuda_stream)
         s.set_equilibrium(1.0, 0.0, 0.0, ERROR_AMP, ERROR_SEED)
         s.step(ERROR_STEPS)
         rho, ux, uy = s.moments()
         torch.cuda.synchronize()
         s.close()
-        path = os.path.join(tmpdir, "%s_%s.npz" % (prec, red))
+        tag = "%s/%s" % (prec, red) + ("/stochastic" if rounding else "")
+        path = os.path.join(tmpdir, tag.replace("/", "_") + ".npz")
         np.savez(path, rho=rho, ux=ux, uy=uy)
-        paths["%s/%s" % (prec, red)] = path
+        paths[tag] = path
     return c, paths
 
 
@@ -754,6 +758,9 @@ FORMS = [
     ("cavity_kn8_128x128x2_p3_nc32_bf16_red_fp64", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "bf16", "fp64"),
     ("cavity_kn8_128x128x2_p3_nc32_bf16_red_comp", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "bf16", "comp"),
     ("cavity_kn8_128x128x2_p3_nc32_fp16_red_fp64", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "fp16", "fp64"),
+    ("cavity_kn8_128x128x2_p3_nc32_fp32", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "fp32", "default"),
+    ("cavity_kn8_128x128x2_p3_nc32_fp32_red_comp", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "fp32", "comp"),
+    ("cavity_kn8_128x128x2_p3_nc32_bf16_stochastic", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "bf16", "comp"),
     ("cavity_unstructured_8192_p4_nc16_fp32", "cavity_kn1_unstructured_8192_p4_nc16x16_fp32", "fp32", "default"),
     ("cavity_kn8_32x32x2_p5_d2q1089_fp32_split", "cavity_kn8_32x32x2_p5_nc33x33_sqrt2_fp32", "fp32", "default"),
 ]
@@ -768,18 +775,22 @@ def measure_forms(args, w, st, value, roof, error):
     by_copy = {}
     for key, wname, prec, red in FORMS:
         wf = dict(WORKLOADS[wname], precision=prec, reduction=red)
+        if key.endswith("_stochastic"):
+            wf["rounding"] = 1
         base = WORKLOADS[wname]["desc"].split(", BF16")[0].split(", FP32")[0]
-        wf["desc"] = "%s [%s state, %s moment sums]" % (base, prec.upper(), red)
+        wf["desc"] = "%s [%s state, %s moment sums%s]" % (base, prec.upper(), red,
+                                                         ", stochastic rounding" if wf.get("rounding") else "")
         forms[key] = measure_form(wf, st, steps, args.warmup, not args.no_tune)
-        by_copy.setdefault(wname, []).append((key, prec, red))
+        by_copy.setdefault(wname, []).append((key, prec, red, wf.get("rounding", 0)))
     if not args.no_error:
         for wname, items in by_copy.items():
             wf = WORKLOADS[wname]
             with tempfile.TemporaryDirectory() as td:
-                copy, paths = gpu_error_moments(wf, [(p, r) for _, p, r in items], st, td)
+                copy, paths = gpu_error_moments(wf, [(p, r, sr) for _, p, r, sr in items], st, td)
                 errs = oracle_errors(copy, paths)
-            for key, prec, red in items:
-                forms[key]["error"] = dict(errs["%s/%s" % (prec, red)], copy=errs["copy"])
+            for key, prec, red, sr in items:
+                tag = "%s/%s" % (prec, red) + ("/stochastic" if sr else "")
+                forms[key]["error"] = dict(errs[tag], copy=errs["copy"])
     bat = measure_batch(WORKLOADS["batch256_couette_cavity_fp32"], st, 10, 3, 2, not args.no_tune)
     forms["batched"] = dict(bat, workload=WORKLOADS["batch256_couette_cavity_fp32"]["desc"])
     forms["implicit_backward_euler"] = measure_implicit(st)
