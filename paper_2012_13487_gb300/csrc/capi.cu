@@ -1723,6 +1723,13 @@ int implicit_step(Batch& b, const fedbm_implicit_params& ip, int nsteps, fedbm_i
     b.time += dt;
     if (!cnt.converged) break;
   }
+  {
+    int word = 0;  // a residual launch whose bounded wait gave up invalidates the step
+    rc = queue_timeout_read(b, g, &word);
+    if (rc) return rc;
+    FEDBM_CK(cudaStreamSynchronize(b.stream));
+    if (word) return timeout_status(word);
+  }
   if (stats) {
     stats->newton_iters = cnt.newton;
     stats->gmres_iters = cnt.gmres;
