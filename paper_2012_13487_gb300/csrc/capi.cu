@@ -87,6 +87,9 @@ int ensure_ops_uploaded(int dev) {
 }
 
 size_t store_bytes(int kind) { return kind == kStoreF64 ? 8 : kind == kStoreF32 ? 4 : 2; }
+
+// Largest dynamic shared memory of one CTA (227 KB on sm_103a).
+constexpr size_t kMaxSmem = 227 * 1024;
 size_t real_bytes(int kind) { return kind == kStoreF64 ? 8 : 4; }
 
 // ---------------------------------------------------------------- aux kernels
@@ -526,7 +529,7 @@ int configure_tc(Batch& b, Group& g) {
   // than its tensor memory serves
   const int max_ctas = 512 / e.tc_tmem_cols(g.Qp);
   smem = std::max(smem, size_t(smem_sm) / size_t(max_ctas + 1) + 1024);
-  FEDBM_CK(e.set_smem_tc(g.store, g.Qp, smem));
+  FEDBM_CK(e.set_smem_tc(g.store, g.Qp, kMaxSmem));
   const int per_sm = e.occupancy_tc(g.store, g.Qp, smem);
   const int by_smem = int(size_t(smem_sm) / smem);
   if (per_sm < 1 || std::max(per_sm, by_smem) * e.tc_tmem_cols(g.Qp) > 512)
@@ -554,8 +557,8 @@ int configure_cluster(Batch& b, Group& g, int ncl) {
   if (smem == 0) return fail(FEDBM_EINVAL, "no velocity-split form for this precision or cluster size "
                                            "(FP64, FP32 or BF16 state; clusters of 2, 4 or 8 CTAs dividing the "
                                            "padded velocity count into multiples of 8)");
-  if (smem > 227 * 1024) return fail(FEDBM_EINVAL, "velocity-split tile does not fit in shared memory");
-  FEDBM_CK(e.set_smem_cl(g.store, smem));
+  if (smem > kMaxSmem) return fail(FEDBM_EINVAL, "velocity-split tile does not fit in shared memory");
+  FEDBM_CK(e.set_smem_cl(g.store, kMaxSmem));
   const int nclusters_max = e.occupancy_cl(g.store, ncl, smem);
   if (nclusters_max < 1) return fail(FEDBM_EINVAL, "velocity-split clusters cannot be resident");
   g.tc = 0;
@@ -578,8 +581,8 @@ int auto_cluster(const Group& g) {
   int best = 0, best_ctas = 0;
   for (int ncl : {2, 4, 8}) {
     const size_t smem = e.cl_smem(g.store, g.Qp, ncl, 1);
-    if (smem == 0 || smem > 227 * 1024) continue;
-    if (e.set_smem_cl(g.store, smem) != cudaSuccess) continue;
+    if (smem == 0 || smem > kMaxSmem) continue;
+    if (e.set_smem_cl(g.store, kMaxSmem) != cudaSuccess) continue;
     const int ctas = e.occupancy_cl(g.store, ncl, smem) * ncl;
     if (ctas > best_ctas) {
       best = ncl;
@@ -591,26 +594,33 @@ int auto_cluster(const Group& g) {
 
 // Tile shape, pipeline depth and persistent grid of a group's stage kernel.
 int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
-  g.tc = 0;
-  g.ncl = 0;
-  g.epc = epc > 0 ? epc : (g.Qp < 128 ? std::max(1, 128 / g.Qp) : 1);
-  g.tpb = tpb > 0 ? tpb : std::min(128, std::max(32, (g.epc * g.Qp + 31) / 32 * 32));
-  if (g.tpb % 32 || g.tpb > 256) return fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256");
+  // the group is changed only once the whole configuration is valid
+  const int e_pc = epc > 0 ? epc : (g.Qp < 128 ? std::max(1, 128 / g.Qp) : 1);
+  const int t_pb = tpb > 0 ? tpb : std::min(128, std::max(32, (e_pc * g.Qp + 31) / 32 * 32));
+  if (t_pb % 32 || t_pb > 256) return fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256");
   if (stages < 0 || stages > 2) return fail(FEDBM_EINVAL, "pipeline_stages must be 0, 1 or 2");
-  g.nstages = stages == 2 ? 2 : 1;
-  g.smem = stage_smem_bytes(g.p, g.store, g.epc, g.Qp, g.nstages);
-  if (g.smem > 227 * 1024 && g.nstages == 2) {
-    g.nstages = 1;
-    g.smem = stage_smem_bytes(g.p, g.store, g.epc, g.Qp, 1);
+  int nst = stages == 2 ? 2 : 1;
+  size_t smem = stage_smem_bytes(g.p, g.store, e_pc, g.Qp, nst);
+  if (smem > kMaxSmem && nst == 2) {
+    nst = 1;
+    smem = stage_smem_bytes(g.p, g.store, e_pc, g.Qp, 1);
   }
-  if (g.smem > 227 * 1024) return fail(FEDBM_EINVAL, "stage tile does not fit in shared memory");
+  if (smem > kMaxSmem) return fail(FEDBM_EINVAL, "stage tile does not fit in shared memory");
   const StageEntry e = stage_entry(g.p);
-  FEDBM_CK(e.set_smem(g.store, g.Qp, g.smem));
+  // the kernel's dynamic shared-memory limit stays at the maximum, so that
+  // groups of one batch sharing this kernel with other tiles keep launching
+  FEDBM_CK(e.set_smem(g.store, g.Qp, kMaxSmem));
   int nsm = 0;
   FEDBM_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device));
-  const int per_sm = e.occupancy(g.store, g.Qp, g.tpb, g.smem);
+  const int per_sm = e.occupancy(g.store, g.Qp, t_pb, smem);
   if (per_sm < 1) return fail(FEDBM_EINVAL, "stage tile cannot be resident on an SM");
-  const int64_t ntiles = (g.K + g.epc - 1) / g.epc;
+  const int64_t ntiles = (g.K + e_pc - 1) / e_pc;
+  g.tc = 0;
+  g.ncl = 0;
+  g.epc = e_pc;
+  g.tpb = t_pb;
+  g.nstages = nst;
+  g.smem = smem;
   g.grid = int(std::min<int64_t>(ntiles, int64_t(per_sm) * nsm));
   g.per_sm = per_sm;
   drop_graphs(b);
@@ -1051,7 +1061,7 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
            const bool want_tc = g.tc_mode > 0;
            // the velocity-split form on request, or when one CTA cannot hold
            // an element's velocities (automatic mode)
-           const bool too_big = stage_smem_bytes(g.p, g.store, std::max(1, epc), g.Qp, 1) > 227 * 1024;
+           const bool too_big = stage_smem_bytes(g.p, g.store, std::max(1, epc), g.Qp, 1) > kMaxSmem;
            const int ncl = g.vsplit >= 2 ? g.vsplit : (g.vsplit == 0 && too_big && !want_tc ? auto_cluster(g) : 0);
            if (ncl >= 2) {
              if ((r = configure_cluster(*b, g, ncl)) != FEDBM_OK) return r;

@@ -81,3 +81,27 @@ def test_autotune_keeps_state_and_uses_cache(tmp_path):
     b2.step(2)
     for c in range(4):
         np.testing.assert_array_equal(b2.state(c), b.state(c))
+
+
+def test_groups_sharing_a_kernel_with_different_tiles_and_failed_retile():
+    """Two groups that use the same compiled stage kernel with different tiles
+    (different shared-memory sizes) both launch, and a rejected re-tile leaves
+    its group as it was."""
+    from paper_2012_13487_gb300 import fedbm as fb
+    c = cases.cavity(4, 3, 3, velset=("nc", 16), kn=1.0)
+    descs = [fb.case_desc(*cases.descriptors(c, "fp32", epc=4, tpb=256)),
+             fb.case_desc(*cases.descriptors(c, "fp32", epc=1, tpb=128))]
+    b = fb.Batch(descs)
+    assert b.info(0).ngroups == 2
+    pr = cases.oracle_problem(c)
+    f0 = cases.initial_state(pr, amp=1e-2, seed=77)
+    for j in range(2):
+        b.set_state(j, f0)
+    with pytest.raises(fb.FedbmError) as e:
+        fb.fedbm_batch_set_tiles(b.h, b.info(1).group, 1, 48, 1)   # not a multiple of 32
+    assert e.value.code == fb.FEDBM_EINVAL
+    assert b.info(1).threads_per_cta == 128
+    b.step(3)
+    f_or = pr.run(f0, 3)
+    for j in range(2):
+        assert cases.rel_max_err(b.state(j), f_or) < 4.0 * pr.Np * 2.0 ** -24 * np.sqrt(15) + 2.0 ** -24
