@@ -625,15 +625,22 @@ def run_ours(args, w, name):
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(3, min(args.steps, 20))
-    f_host = torch.empty((K, Np, Q), dtype=torch.float64).pin_memory()
-    s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
     from paper_2012_13487_gb300 import fedbm as fb
-    fb.fedbm_get_state(s.h, f_host, False)
+    # the host state in the solver's natural input precision: FP64 for the FP64
+    # form, FP32 (fedbm_set_state_f32) for the FP32 and 16-bit forms
+    in_f32 = w["precision"] != "fp64"
+    set_state = fb.fedbm_set_state_f32 if in_f32 else fb.fedbm_set_state
+    in_dtype = torch.float32 if in_f32 else torch.float64
+    s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 201213487)
+    f64 = torch.empty((K, Np, Q), dtype=torch.float64).pin_memory()
+    fb.fedbm_get_state(s.h, f64, False)
+    f_host = f64.to(in_dtype).pin_memory()
+    del f64
     rho = torch.empty((K, Np), dtype=torch.float64).pin_memory()
     ux = torch.empty_like(rho).pin_memory()
     uy = torch.empty_like(rho).pin_memory()
     for _ in range(2):
-        fb.fedbm_set_state(s.h, f_host, False)
+        set_state(s.h, f_host, False)
         fb.fedbm_rk_step(s.h, 1)
         fb.fedbm_get_moments(s.h, rho, ux, uy, False)
     # (a) serial: the library's host path (copy into its staging buffer, encode,
@@ -642,7 +649,7 @@ def run_ours(args, w, name):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        fb.fedbm_set_state(s.h, f_host, False)
+        set_state(s.h, f_host, False)
         fb.fedbm_rk_step(s.h, 1)
         fb.fedbm_get_moments(s.h, rho, ux, uy, False)
     torch.cuda.synchronize()
@@ -654,7 +661,7 @@ def run_ours(args, w, name):
     # while step i is encoded, stepped and read out; every step's copy and
     # read-out stay inside the timed region
     cs = torch.cuda.Stream()
-    d_in = [torch.empty((K, Np, Q), dtype=torch.float64, device="cuda") for _ in range(2)]
+    d_in = [torch.empty((K, Np, Q), dtype=in_dtype, device="cuda") for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
 
@@ -671,7 +678,7 @@ def run_ours(args, w, name):
             if i + 1 < n:
                 enqueue_copy((i + 1) % 2)
             st.wait_event(copied[j])
-            fb.fedbm_set_state(s.h, d_in[j], True)
+            set_state(s.h, d_in[j], True)
             consumed[j].record(st)
             fb.fedbm_rk_step(s.h, 1)
             fb.fedbm_get_moments(s.h, rho, ux, uy, False)
@@ -731,12 +738,14 @@ def run_ours(args, w, name):
             "error": error,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "DOF-stage/s", "steps": e2e_steps,
-                    "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": 3 * K * Np * 8,
-                    "path": "pinned host FP64 -> device buffer on a copy stream (step i+1's copy overlaps "
-                            "step i) + fedbm_set_state(device) + fedbm_rk_step(1) + fedbm_get_moments(host)",
+                    "h2d_bytes_per_step": dof * (4 if in_f32 else 8), "d2h_bytes_per_step": 3 * K * Np * 8,
+                    "input_dtype": "f32" if in_f32 else "f64",
+                    "path": "pinned host %s state -> device buffer on a copy stream (step i+1's copy overlaps "
+                            "step i) + %s(device) + fedbm_rk_step(1) + fedbm_get_moments(host, FP64)"
+                            % ("FP32" if in_f32 else "FP64", set_state.__name__),
                     "serial": {"value": serial_value, "unit": "DOF-stage/s",
-                               "path": "fedbm_set_state(host FP64) + fedbm_rk_step(1) + fedbm_get_moments(host), "
-                                       "one step after the other"}},
+                               "path": "%s(host) + fedbm_rk_step(1) + fedbm_get_moments(host), "
+                                       "one step after the other" % set_state.__name__}},
             "gpu_launches": 5 * args.steps * args.repeats,
             "clocks": clocks,
             "mass_after": mass,

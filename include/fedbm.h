@@ -234,6 +234,12 @@ void fedbm_destroy(fedbm_solver* s);
  * device input; host input is copied before the call returns. */
 int fedbm_set_state(fedbm_solver* s, const double* f, int32_t on_device);
 
+/* The same from a canonical FP32 state float f[K][Np][Q] (host or device):
+ * for FP32 storage each value is stored as given, so a caller whose data are
+ * FP32 moves half the bytes of the FP64 call; the deviation forms encode from
+ * the FP32 values in FP64 as fedbm_set_state does. */
+int fedbm_set_state_f32(fedbm_solver* s, const float* f, int32_t on_device);
+
 /* f_i = f_i^eq(rho0, u0) * (1 + amp * u), u in [-1, 1) drawn by SplitMix64 at
  * canonical index (k*Np + j)*Q + i of seed (a seeded perturbation of an
  * equilibrium, computed on the device).  Resets time and step count. */
@@ -355,6 +361,7 @@ int fedbm_batch_create(const fedbm_case_desc* cases, int32_t ncases, void* cuda_
 void fedbm_batch_destroy(fedbm_batch* b);
 /* Per-case counterparts of the solver calls (case c, 0 <= c < ncases). */
 int fedbm_batch_set_state(fedbm_batch* b, int32_t c, const double* f, int32_t on_device);
+int fedbm_batch_set_state_f32(fedbm_batch* b, int32_t c, const float* f, int32_t on_device);
 int fedbm_batch_set_equilibrium(fedbm_batch* b, int32_t c, double rho0, double ux0, double uy0,
                                 double amp, uint64_t seed);
 int fedbm_batch_get_state(fedbm_batch* b, int32_t c, double* f, int32_t on_device);

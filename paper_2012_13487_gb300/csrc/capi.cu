@@ -119,13 +119,14 @@ __global__ void equilibrium_kernel(double* out, const double* vel64, int64_t K, 
   }
 }
 
-// canonical FP64 [K][Np][Q] -> internal storage [K][Np][Qp] (one CTA per element)
-template <class ST>
-__global__ void encode_kernel(const double* in, void* out, float* scale, const double* vel64, int Np, int Q,
+// canonical FP64 or FP32 [K][Np][Q] -> internal storage [K][Np][Qp] (one CTA
+// per element; the deviation forms compute their scale and codes in FP64)
+template <class ST, typename TIn>
+__global__ void encode_kernel(const TIn* in, void* out, float* scale, const double* vel64, int Np, int Q,
                               int Qp) {
   using S = typename ST::S;
   const int64_t k = blockIdx.x;
-  const double* src = in + k * Np * Q;
+  const TIn* src = in + k * Np * Q;
   S* dst = static_cast<S*>(out) + k * Np * Qp;
   const double* w = vel64 + 2 * Qp;
   if constexpr (ST::dev) {
@@ -133,7 +134,7 @@ __global__ void encode_kernel(const double* in, void* out, float* scale, const d
     float m = 0.f;
     for (int j = threadIdx.x; j < Np * Q; j += blockDim.x) {
       const int i = j % Q;
-      if (w[i] > 0) m = fmaxf(m, float(fabs((src[j] - w[i]) / w[i])));
+      if (w[i] > 0) m = fmaxf(m, float(fabs((double(src[j]) - w[i]) / w[i])));
     }
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -155,7 +156,7 @@ __global__ void encode_kernel(const double* in, void* out, float* scale, const d
     for (int j = threadIdx.x; j < Np * Qp; j += blockDim.x) {
       const int n = j / Qp, i = j % Qp;
       float q = 0.f;
-      if (i < Q && w[i] > 0) q = float((src[n * Q + i] - w[i]) / w[i] * inv_s);
+      if (i < Q && w[i] > 0) q = float((double(src[n * Q + i]) - w[i]) / w[i] * inv_s);
       dst[j] = ST::from_r(q);
     }
   } else {
@@ -163,7 +164,7 @@ __global__ void encode_kernel(const double* in, void* out, float* scale, const d
     (void)w;
     for (int j = threadIdx.x; j < Np * Qp; j += blockDim.x) {
       const int n = j / Qp, i = j % Qp;
-      dst[j] = S(i < Q ? src[n * Q + i] : 0.0);
+      dst[j] = S(i < Q ? double(src[n * Q + i]) : 0.0);
     }
   }
 }
@@ -1110,17 +1111,18 @@ int timeout_status(int word) {
 }
 
 // canonical FP64 (device) -> internal state of case c
-int encode_case(Batch& b, int c, const double* src) {
+template <typename TIn>
+int encode_case(Batch& b, int c, const TIn* src) {
   const Case& cs = b.cases[c];
   const Group& g = b.groups[cs.group];
   const size_t off = size_t(cs.k_off) * g.Np * g.Qp;
   float* sc = g.scale[b.cur] ? g.scale[b.cur] + cs.k_off : nullptr;
   const int blk = 256;
   switch (g.store) {
-    case kStoreF64: encode_kernel<StoreF64><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<double*>(g.f[b.cur]) + off, nullptr, g.vel64, g.Np, g.Q, g.Qp); break;
-    case kStoreF32: encode_kernel<StoreF32><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<float*>(g.f[b.cur]) + off, nullptr, g.vel64, g.Np, g.Q, g.Qp); break;
-    case kStoreBF16: encode_kernel<StoreBF16><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__nv_bfloat16*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
-    default: encode_kernel<StoreF16><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__half*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
+    case kStoreF64: encode_kernel<StoreF64, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<double*>(g.f[b.cur]) + off, nullptr, g.vel64, g.Np, g.Q, g.Qp); break;
+    case kStoreF32: encode_kernel<StoreF32, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<float*>(g.f[b.cur]) + off, nullptr, g.vel64, g.Np, g.Q, g.Qp); break;
+    case kStoreBF16: encode_kernel<StoreBF16, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__nv_bfloat16*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
+    default: encode_kernel<StoreF16, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__half*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
   }
   FEDBM_CK(cudaGetLastError());
   // a new state starts with a clear stage-kernel timeout word (and the
@@ -1132,18 +1134,20 @@ int encode_case(Batch& b, int c, const double* src) {
   return FEDBM_OK;
 }
 
-int set_state(Batch& b, int c, const double* f, int on_device) {
+// canonical state (FP64, or FP32 for fedbm_set_state_f32) -> internal state
+template <typename TIn>
+int set_state(Batch& b, int c, const TIn* f, int on_device) {
   NvtxRange nvtx("fedbm set_state");
   if (!f) return fail(FEDBM_EINVAL, "null state pointer");
   const Case& cs = b.cases[c];
   const Group& g = b.groups[cs.group];
   const size_t n = size_t(cs.K) * g.Np * g.Q;
-  const double* src = f;
+  const TIn* src = f;
   if (!on_device) {
-    int rc = ensure_staging(b, n);
+    int rc = ensure_staging(b, n);  // n doubles hold n values of either type
     if (rc) return rc;
-    FEDBM_CK(cudaMemcpyAsync(b.staging, f, n * sizeof(double), cudaMemcpyHostToDevice, b.stream));
-    src = b.staging;
+    FEDBM_CK(cudaMemcpyAsync(b.staging, f, n * sizeof(TIn), cudaMemcpyHostToDevice, b.stream));
+    src = reinterpret_cast<const TIn*>(b.staging);
   }
   int rc = encode_case(b, c, src);
   if (rc) return rc;
@@ -1160,7 +1164,7 @@ int set_equilibrium(Batch& b, int c, double rho0, double ux0, double uy0, double
   equilibrium_kernel<<<grid_for(n, 256), 256, 0, b.stream>>>(b.staging, g.vel64, cs.K, g.Np, g.Q, g.Qp, rho0, ux0, uy0,
                                                              amp, seed, g.vd.eq_order);
   FEDBM_CK(cudaGetLastError());
-  return encode_case(b, c, b.staging);
+  return encode_case(b, c, static_cast<const double*>(b.staging));
 }
 
 template <class ST>
@@ -1869,6 +1873,11 @@ extern "C" int fedbm_set_state(fedbm_solver* s, const double* f, int32_t on_devi
   return set_state(B, 0, f, on_device);
 }
 
+extern "C" int fedbm_set_state_f32(fedbm_solver* s, const float* f, int32_t on_device) {
+  FEDBM_SOLVER(s);
+  return set_state(B, 0, f, on_device);
+}
+
 extern "C" int fedbm_set_equilibrium(fedbm_solver* s, double rho0, double ux0, double uy0, double amp,
                                      uint64_t seed) {
   FEDBM_SOLVER(s);
@@ -1949,6 +1958,11 @@ extern "C" void fedbm_batch_destroy(fedbm_batch* h) {
   } while (0)
 
 extern "C" int fedbm_batch_set_state(fedbm_batch* h, int32_t c, const double* f, int32_t on_device) {
+  FEDBM_BATCH(h, c);
+  return set_state(B, c, f, on_device);
+}
+
+extern "C" int fedbm_batch_set_state_f32(fedbm_batch* h, int32_t c, const float* f, int32_t on_device) {
   FEDBM_BATCH(h, c);
   return set_state(B, c, f, on_device);
 }

@@ -100,6 +100,8 @@ SIGNATURES = {
                                     ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
     "fedbm_destroy": (None, [_P]),
     "fedbm_set_state": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "fedbm_set_state_f32": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "fedbm_batch_set_state_f32": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     "fedbm_set_equilibrium": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_uint64]),
     "fedbm_rk_step": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -274,6 +276,14 @@ def fedbm_destroy(h):
 
 def fedbm_set_state(h, f, on_device):
     _check(lib().fedbm_set_state(h, _ptr(f), int(on_device)))
+
+
+def fedbm_set_state_f32(h, f, on_device):
+    _check(lib().fedbm_set_state_f32(h, _ptr(f), int(on_device)))
+
+
+def fedbm_batch_set_state_f32(h, c, f, on_device):
+    _check(lib().fedbm_batch_set_state_f32(h, c, _ptr(f), int(on_device)))
 
 
 def fedbm_set_equilibrium(h, rho0=1.0, ux0=0.0, uy0=0.0, amp=0.0, seed=0):

@@ -305,3 +305,26 @@ def test_full_size_couette_p5_gh16_sampled_two_stages():
     tol = fp32_tol(pr, 2) * np.abs(f0).max()
     assert np.abs(f1_gpu[sample] - f1[sample]).max() <= tol
     assert np.abs(f2_gpu[sample] - f2_s).max() <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64"])
+def test_set_state_from_fp32_input(prec):
+    """fedbm_set_state_f32 stores an FP32 state as fedbm_set_state stores the
+    same values given in FP64 (bit for bit), from host and from device memory."""
+    import torch
+
+    from paper_2012_13487_gb300 import fedbm as fb
+    c = cases.cavity(4, 3, 3, velset=("nc", 8), kn=1.0)
+    pr = cases.oracle_problem(c)
+    f32 = cases.initial_state(pr, amp=1e-2, seed=19).astype(np.float32)
+    a = cases.solver(c, prec)
+    a.set_state(f32.astype(np.float64))
+    a.step(2)
+    want = a.state()
+    for on_device in (False, True):
+        b = cases.solver(c, prec)
+        src = torch.from_numpy(f32).cuda() if on_device else np.ascontiguousarray(f32)
+        fb.fedbm_set_state_f32(b.h, src, on_device)
+        torch.cuda.synchronize()
+        b.step(2)
+        assert np.array_equal(b.state(), want)
