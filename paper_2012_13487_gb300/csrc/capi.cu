@@ -639,11 +639,20 @@ int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
 // element count) in a flat JSON object, one entry per line.
 struct TuneEntry {
   int epc = 0, tpb = 0, stages = 0, tc = 0;
+  int ncl = 0;  // > 1: the velocity-split form with clusters of ncl CTAs
   double us = 0;
 };
 
 int apply_tune(Batch& b, Group& g, const TuneEntry& t) {
+  if (t.ncl > 1) return configure_cluster(b, g, t.ncl);
   return t.tc ? configure_tc(b, g) : configure_tiles(b, g, t.epc, t.tpb, t.stages);
+}
+
+// The velocity-split form can serve this group with clusters of ncl CTAs.
+bool cluster_available(const Group& g, int ncl) {
+  if (g.vsplit == 1) return false;  // the caller ruled the form out
+  const size_t smem = stage_entry(g.p).cl_smem(g.store, g.Qp, ncl, 1);
+  return smem > 0 && smem <= kMaxSmem;
 }
 
 std::string tune_key(const Batch& b, const Group& g) {
@@ -664,8 +673,8 @@ std::vector<std::pair<std::string, TuneEntry>> read_tune_cache(const char* path)
   while (std::fgets(line, sizeof(line), fp)) {
     char key[512];
     TuneEntry t;
-    if (std::sscanf(line, " \"%511[^\"]\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"tc\": %d, \"us\": %lf}", key,
-                    &t.epc, &t.tpb, &t.stages, &t.tc, &t.us) == 6)
+    if (std::sscanf(line, " \"%511[^\"]\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"tc\": %d, \"ncl\": %d, \"us\": %lf}",
+                    key, &t.epc, &t.tpb, &t.stages, &t.tc, &t.ncl, &t.us) == 7)
       out.emplace_back(key, t);
   }
   std::fclose(fp);
@@ -678,9 +687,10 @@ void write_tune_cache(const char* path, const std::vector<std::pair<std::string,
   if (!fp) return;
   std::fprintf(fp, "{\n");
   for (size_t j = 0; j < entries.size(); ++j)
-    std::fprintf(fp, "\"%s\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"tc\": %d, \"us\": %.3f}%s\n",
+    std::fprintf(fp, "\"%s\": {\"epc\": %d, \"tpb\": %d, \"stages\": %d, \"tc\": %d, \"ncl\": %d, \"us\": %.3f}%s\n",
                  entries[j].first.c_str(), entries[j].second.epc, entries[j].second.tpb, entries[j].second.stages,
-                 entries[j].second.tc, entries[j].second.us, j + 1 < entries.size() ? "," : "");
+                 entries[j].second.tc, entries[j].second.ncl, entries[j].second.us,
+                 j + 1 < entries.size() ? "," : "");
   std::fprintf(fp, "}\n");
   std::fclose(fp);
 }
@@ -704,7 +714,7 @@ int autotune(Batch& b, const char* cache_path, int trials) {
     const TuneEntry* hit = nullptr;
     for (auto& kv : cache)
       if (kv.first == key) hit = &kv.second;
-    if (hit && (!hit->tc || tc_available(g))) {
+    if (hit && (!hit->tc || tc_available(g)) && (hit->ncl < 2 || cluster_available(g, hit->ncl))) {
       if ((rc = apply_tune(b, g, *hit)) != FEDBM_OK) break;
       g.tune_us = hit->us;
       continue;
@@ -749,6 +759,17 @@ int autotune(Batch& b, const char* cache_path, int trials) {
       cand.tpb = g.Qp;
       cand.stages = 1;
       cand.tc = 1;
+      time_current(cand);
+    }
+    // the velocity-split form where the velocity count is large enough that
+    // a smaller per-CTA slice may let more CTAs share an SM
+    for (int ncl : {2, 4}) {
+      if (g.Qp < 256 || !cluster_available(g, ncl) || configure_cluster(b, g, ncl) != FEDBM_OK) continue;
+      TuneEntry cand;
+      cand.epc = 1;
+      cand.tpb = 256;
+      cand.stages = 1;
+      cand.ncl = ncl;
       time_current(cand);
     }
     cudaGetLastError();

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, cl_min_blocks<ST>()) stage_kernel_cl
   const size_t row_bytes = size_t(Qc) * sizeof(S);
   const size_t rrow_bytes = size_t(Qc) * sizeof(R);
   const int64_t ntiles = (a.K + epc - 1) / epc;
-  constexpr bool kImm = kHaveOpsTable && sizeof(R) == 4 && P <= 4;
+  constexpr bool kImm = kHaveOpsTable && sizeof(R) == 4 && P <= 5;
 
   for (int v = tid; v < 3 * Qc; v += nth) s_vel[v] = a.vel[(v / Qc) * Qp + v0 + v % Qc];
   if (tid == 0) {
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, cl_min_blocks<ST>()) stage_kernel_cl
       for (int item = tid; item < ne * Qc; item += nth) {
         const int e = item / Qc, i = item - e * Qc, ig = v0 + i;
         const R ex = s_vel[i], ey = s_vel[Qc + i];
-        const R w = ST::dev ? s_vel[2 * Qc + i] : a.vel[kVelW * Qp + ig];
+        const R w = s_vel[2 * Qc + i];
         const R* g = s_geo + e * kGeoStrideDev;
         const R dt = g[kGeoDt], inv_tau = g[kGeoInvTau];
         const R ar = ex * g[0] + ey * g[2], as = ex * g[1] + ey * g[3];

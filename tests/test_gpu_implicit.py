@@ -130,3 +130,21 @@ def test_backward_euler_on_other_meshes_and_forms(form):
     s.implicit_step(_tight(0, dt), 1)
     f_or, _ = implicit.sdirk_step(pr, f0, dt, "be")
     assert cases.rel_max_err(s.state(), f_or) < 1e-10
+
+
+def test_backward_euler_steady_cavity_matches_oracle_steady_state():
+    """The paper's cavity route (backward Euler to the steady state) on a small
+    Kn = 2 cavity, against the oracle's own steady solver (pseudo-time Newton
+    with a dense Jacobian taken once): the two steady states agree."""
+    c = cases.cavity(2, 2, 2, velset=("gh", 3), kn=2.0, U=0.1)
+    pr = cases.oracle_problem(c)
+    fs, res = dg.steady_state(pr, pr.equilibrium_state())
+    assert res < 1e-11
+    s = cases.solver(c, "fp64")
+    s.set_equilibrium(1.0, 0.0, 0.0, 0.0, 0)
+    st = s.implicit_step(_tight(0, 50.0, newton_rtol=1e-10, newton_atol=1e-13, gmres_rtol=1e-8,
+                                gmres_restart=120, gmres_max_iter=4000), 30)
+    print("steady cavity: Newton %d GMRES %d" % (st.newton_iters, st.gmres_iters))
+    f = s.state()
+    assert np.abs(pr.rhs(f)).max() < 1e-9
+    assert np.abs(f - fs).max() < 1e-8
