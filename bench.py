@@ -59,6 +59,9 @@ WORKLOADS = {
         desc="lid-driven cavity Kn=8, 128x128x2 triangles, p=3, NC 32x32, BF16 deviation state, FP64 moments",
         reduction="fp64"),
 }
+WORKLOADS["cavity_kn2_64x64x2_p4_nc16x16_fp32"] = dict(
+    kind="cavity", nx=64, ny=64, p=4, vel=("nc", 16), kn=2.0, speed=0.1, precision="fp32",
+    desc="lid-driven cavity Kn=2, 64x64x2 triangles, p=4, NC 16x16 on [-4,4]sqrt(RT), lid 0.1, FP32")
 WORKLOADS["cavity_kn1_unstructured_8192_p4_nc16x16_fp32"] = dict(
     kind="cavity", nx=64, ny=64, p=4, vel=("nc", 16), kn=1.0, speed=0.1, precision="fp32",
     unstructured=True, mesh_seed=201213487,
@@ -762,6 +765,7 @@ FORMS = [
     ("fp32_red_fp64", DEFAULT_WORKLOAD, "fp32", "fp64"),
     ("fp32_red_comp", DEFAULT_WORKLOAD, "fp32", "comp"),
     ("bf16_state", DEFAULT_WORKLOAD, "bf16", "default"),
+    ("cavity_kn2_64x64x2_p4_nc16_fp32", "cavity_kn2_64x64x2_p4_nc16x16_fp32", "fp32", "default"),
     ("couette_256x256x2_p5_gh16_fp32", "couette_kn1_256x256x2_p5_gh16_fp32", "fp32", "default"),
     ("couette_256x256x2_p5_gh16_bf16", "couette_kn1_256x256x2_p5_gh16_bf16", "bf16", "default"),
     ("cavity_kn8_128x128x2_p3_nc32_bf16_red_fp64", "cavity_kn8_128x128x2_p3_nc32x32_bf16", "bf16", "fp64"),
