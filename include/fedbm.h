@@ -372,7 +372,9 @@ int fedbm_batch_info(const fedbm_batch* b, int32_t c, fedbm_info_t* info);
 /* Advance every case nsteps LSRK(5,4) steps (one graph launch per step). */
 int fedbm_batch_rk_step(fedbm_batch* b, int32_t nsteps);
 /* Re-tile one group's stage kernel as the FMA form (0 = automatic for each
- * argument); used by the tile autotuner.  Takes effect from the next step. */
+ * argument); used by the tile autotuner.  Takes effect from the next step.
+ * On EINVAL (a tile that is not valid or does not fit shared memory) the group
+ * keeps its current form and tile. */
 int fedbm_batch_set_tiles(fedbm_batch* b, int32_t group, int32_t elems_per_cta,
                           int32_t threads_per_cta, int32_t pipeline_stages);
 /* Switch one group's stage kernel to the tensor-core form (on = 1; EINVAL if
@@ -382,9 +384,11 @@ int fedbm_batch_set_tensor_cores(fedbm_batch* b, int32_t group, int32_t on);
 
 /* Tile autotuner: for every kernel group, time each candidate stage-kernel
  * tile (elements per CTA 1..32, threads per CTA 64/128/256, one or two
- * pipeline stages, and the tensor-core form where the group has it and was
- * not created with tensor_cores = -1) on `trials` launches (0 means 5) and
- * keep the fastest.
+ * pipeline stages, the tensor-core form where the group has it and was not
+ * created with tensor_cores = -1, and from 256 padded velocities up the
+ * velocity-split form with clusters of 2 and 4 CTAs unless velocity_split = 1)
+ * on `trials` launches (0 means 5) and keep the fastest.  Groups that use the
+ * velocity-split form because no FMA tile fits keep it.
  * The current state is left unchanged.  With a cache_path (NULL or "" for
  * none), results are read from and written to a JSON object keyed by device
  * name, degree, padded velocity count, precision, reduction and element
