@@ -213,7 +213,7 @@ def make_descriptors(w, epc=0, tpb=0, stages=0, tc=0):
                        nc_sqrt2=w.get("nc_sqrt2", 0))
     prm = fb.params(kn=w["kn"], precision=PREC[w["precision"]], reduction=RED[w.get("reduction", "default")],
                     cfl=0.5, elems_per_cta=epc, threads_per_cta=tpb, pipeline_stages=stages, tensor_cores=tc,
-                    rounding=w.get("rounding", 0))
+                    rounding=w.get("rounding", 0), velocity_split=w.get("velocity_split", 0))
     return m, v, prm
 
 
