@@ -817,23 +817,27 @@ def measure_implicit(st):
     import torch
     from paper_2012_13487_gb300 import fedbm as fb
     w = dict(kind="couette", nx=16, ny=16, p=3, vel=("gh", 4), kn=1.0, speed=0.1, precision="fp64")
-    s = make_solver(w, st.cuda_stream)
-    s.set_equilibrium(1.0, 0.0, 0.0, 1e-3, 201213487)
-    ip = fb.implicit_params(fb.IMPLICIT_BE, 0.5, newton_rtol=1e-8, newton_atol=1e-12, gmres_rtol=1e-3,
-                            gmres_restart=40, gmres_max_iter=4000)
-    s.implicit_step(ip, 1)            # warm-up (work space, first launches)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    stats = s.implicit_step(ip, 3)
-    torch.cuda.synchronize()
-    secs = time.perf_counter() - t0
     K, Np, Q = dims(w)
-    s.close()
-    return {"value": stats.rhs_evals * K * Np * Q / secs, "unit": "DOF-residual evaluations/s",
+    out = {}
+    for pc in (1, 0):
+        s = make_solver(w, st.cuda_stream)
+        s.set_equilibrium(1.0, 0.0, 0.0, 1e-3, 201213487)
+        ip = fb.implicit_params(fb.IMPLICIT_BE, 0.5, newton_rtol=1e-8, newton_atol=1e-12, gmres_rtol=1e-3,
+                                gmres_restart=40, gmres_max_iter=4000, preconditioner=pc)
+        s.implicit_step(ip, 1)            # warm-up (work space, preconditioner, first launches)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = s.implicit_step(ip, 3)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        s.close()
+        out["block_jacobi" if pc else "no_preconditioner"] = {
+            "value": stats.rhs_evals * K * Np * Q / secs, "unit": "DOF-residual evaluations/s",
             "s_per_step": secs / 3, "newton_iters": stats.newton_iters, "gmres_iters": stats.gmres_iters,
-            "rhs_evals": stats.rhs_evals, "converged": bool(stats.converged),
-            "workload": "Couette Kn=1, 16x16x2 triangles, p=3, GH D2Q16, FP64; backward Euler dt = 0.5, "
-                        "3 steps, Newton to 1e-8 relative, GMRES(40) forcing 1e-3, no preconditioner"}
+            "rhs_evals": stats.rhs_evals, "converged": bool(stats.converged)}
+    out["workload"] = ("Couette Kn=1, 16x16x2 triangles, p=3, GH D2Q16, FP64; backward Euler dt = 0.5, 3 steps, "
+                       "Newton to 1e-8 relative, GMRES(40) forcing 1e-3")
+    return out
 
 
 def run_batch_workload(args, w, name, st, world, rank, dist):

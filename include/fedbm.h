@@ -272,8 +272,9 @@ int fedbm_rk_stage(fedbm_solver* s, int32_t stage);
  * Stage i solves Y_i = u_n + dt sum_{j<i} a_ij k_j + dt gamma R(Y_i) by
  * Newton's method, k_i = (Y_i - base_i)/(dt gamma), u_{n+1} = u_n + dt sum b_i k_i.
  * Each Newton correction solves (I - dt gamma J) d = -G with restarted
- * GMRES(m) (classical Gram-Schmidt with re-orthogonalisation, no
- * preconditioner), J v = (R(Y + e v) - R(Y)) / e matrix-free; every R is one
+ * GMRES(m) (classical Gram-Schmidt with re-orthogonalisation, optionally right
+ * preconditioned by element-and-velocity block Jacobi), J v =
+ * (R(Y + e v) - R(Y)) / e matrix-free; every R is one
  * launch of the fused stage kernel.  Vectors are FP64 in the device layout;
  * R runs in the solver's precision (FP64 or FP32 state only). */
 enum fedbm_implicit_scheme {
@@ -295,6 +296,12 @@ typedef struct fedbm_implicit_params {
   int32_t gmres_restart;   /* m (1..200); 0 means 30                              */
   int32_t gmres_max_iter;  /* per Newton correction; 0 means 1000                 */
   double  gmres_rtol;      /* forcing term: |J d + G| <= rtol |G|; 0 means 1e-4   */
+  int32_t preconditioner;  /* 0: none; 1: element-and-velocity block Jacobi (right
+                              preconditioning by the inverse of each element's
+                              own-node block of I - dt gamma J at each velocity:
+                              transport within the element, the element's own
+                              upwind face traces and the 1/tau relaxation;
+                              built once per dt gamma, K Np^2 Qp doubles) */
 } fedbm_implicit_params;
 typedef struct fedbm_implicit_stats {
   int32_t newton_iters;    /* Newton corrections over all stages and steps        */

@@ -1488,11 +1488,17 @@ struct Implicit {
   void* r32 = nullptr;        // FP32 state: FP32 residual register
   void* scratch = nullptr;    // stage-kernel state output (unused values)
   void* geo_unit = nullptr;   // geometry with dt = 1
+  // element-and-velocity block-Jacobi preconditioner (right preconditioning)
+  double* minv = nullptr;     // [K][Np][Np][Qp] block inverses of (I - dt gamma J)
+  double* z = nullptr;        // M^-1 v
+  double* ops = nullptr;      // FP64 Dr | Ds | LIFT of the degree
+  int* fmask = nullptr;       // [3][Nfp]
+  double minv_dtg = 0;        // dt gamma the inverses were built for (0 = none)
 };
 
 void free_implicit(Implicit& im) {
   void* bufs[] = {im.u0, im.Y, im.base, im.RY, im.G, im.d, im.w, im.Yp, im.Rp, im.V, im.k, im.partial, im.hdev,
-                  im.x32, im.r32, im.scratch, im.geo_unit};
+                  im.x32, im.r32, im.scratch, im.geo_unit, im.minv, im.z, im.ops, im.fmask};
   for (void* p : bufs) cudaFree(p);
   im = Implicit();
 }
@@ -1520,6 +1526,26 @@ int ensure_implicit(const Batch& b, const Group& g, Implicit& im, int m, int s) 
   FEDBM_CK(cudaMalloc(&im.geo_unit, size_t(g.K) * kGeoStrideDev * rb));
   FEDBM_CK(cudaMemcpyAsync(im.geo_unit, g.geo, size_t(g.K) * kGeoStrideDev * rb, cudaMemcpyDeviceToDevice, b.stream));
   FEDBM_CK(krylov::set_geo_dt(g.K, kGeoStrideDev, kGeoDt, 1.0, im.geo_unit, int(rb), b.stream));
+  return FEDBM_OK;
+}
+
+// The block-Jacobi inverses for this dt gamma (built on first use, rebuilt
+// when dt gamma changes).
+int ensure_block_jacobi(const Batch& b, const Group& g, Implicit& im, double dtg) {
+  if (im.minv && im.minv_dtg == dtg) return FEDBM_OK;
+  if (!im.minv) {
+    FEDBM_CK(cudaMalloc(&im.minv, size_t(im.n) * g.Np * sizeof(double)));
+    FEDBM_CK(cudaMalloc(&im.z, size_t(im.n) * sizeof(double)));
+    std::vector<double> ops(g.ops.Dr);
+    ops.insert(ops.end(), g.ops.Ds.begin(), g.ops.Ds.end());
+    ops.insert(ops.end(), g.ops.LIFT.begin(), g.ops.LIFT.end());
+    int rc = upload_vec(ops, reinterpret_cast<void**>(&im.ops));
+    if (rc) return rc;
+    if ((rc = upload_vec(g.ops.fmask, reinterpret_cast<void**>(&im.fmask))) != FEDBM_OK) return rc;
+  }
+  FEDBM_CK(krylov::block_jacobi_build(g.K, g.Np, g.Nfp, g.Qp, g.geo, int(real_bytes(g.store)), g.vel64, im.ops,
+                                      im.fmask, dtg, 2.0 * g.beta - 1.0, im.minv, b.stream));
+  im.minv_dtg = dtg;
   return FEDBM_OK;
 }
 
@@ -1571,7 +1597,7 @@ struct ImplicitCounters {
 // classical Gram-Schmidt with one re-orthogonalisation; J v is taken as
 // (R(Y + eps v) - R(Y)) / eps.  Stops when the residual is <= tol.
 int implicit_gmres(const Batch& b, const Group& g, Implicit& im, double dtg, double eps, double tol, int max_iter,
-                   ImplicitCounters& cnt) {
+                   bool precond, ImplicitCounters& cnt) {
   const int64_t n = im.n;
   const int m = im.m;
   cudaStream_t st = b.stream;
@@ -1609,12 +1635,21 @@ int implicit_gmres(const Batch& b, const Group& g, Implicit& im, double dtg, dou
     double resid = beta;
     for (int j = 0; j < m && total < max_iter; ++j, ++total) {
       double* vj = im.V + size_t(j) * n;
-      // w = A v_j
-      FEDBM_CK(krylov::axpby(n, 1.0, im.Y, eps, vj, im.Yp, st));
+      // w = A M^-1 v_j (right preconditioning; M = I without a preconditioner)
+      const double* xj = vj;
+      double ex = eps;
+      if (precond) {
+        FEDBM_CK(krylov::block_jacobi_apply(g.K, g.Np, g.Qp, im.minv, vj, im.z, st));
+        double zn = 0;
+        if ((rc = implicit_norm(b, im, im.z, &zn)) != FEDBM_OK) return rc;
+        xj = im.z;
+        ex = zn > 0 ? eps / zn : eps;
+      }
+      FEDBM_CK(krylov::axpby(n, 1.0, im.Y, ex, xj, im.Yp, st));
       if ((rc = implicit_rhs(b, g, im, im.Yp, im.Rp)) != FEDBM_OK) return rc;
       ++cnt.rhs;
       FEDBM_CK(krylov::axpby(n, 1.0, im.Rp, -1.0, im.RY, im.w, st));
-      FEDBM_CK(krylov::axpby(n, 1.0, vj, -dtg / eps, im.w, im.w, st));
+      FEDBM_CK(krylov::axpby(n, 1.0, xj, -dtg / ex, im.w, im.w, st));
       // two passes of classical Gram-Schmidt against v_0 .. v_j
       for (int pass = 0; pass < 2; ++pass) {
         std::vector<double>& hh = pass == 0 ? h1 : h2;
@@ -1657,7 +1692,14 @@ int implicit_gmres(const Batch& b, const Group& g, Implicit& im, double dtg, dou
       y[i] = H[size_t(i) * m + i] != 0.0 ? acc / H[size_t(i) * m + i] : 0.0;
     }
     FEDBM_CK(cudaMemcpyAsync(im.hdev, y.data(), size_t(jend) * sizeof(double), cudaMemcpyHostToDevice, st));
-    FEDBM_CK(krylov::add_combination(n, jend, im.V, im.hdev, im.d, st));
+    if (precond) {  // d += M^-1 (V y)
+      FEDBM_CK(cudaMemsetAsync(im.w, 0, size_t(n) * sizeof(double), st));
+      FEDBM_CK(krylov::add_combination(n, jend, im.V, im.hdev, im.w, st));
+      FEDBM_CK(krylov::block_jacobi_apply(g.K, g.Np, g.Qp, im.minv, im.w, im.z, st));
+      FEDBM_CK(krylov::axpby(n, 1.0, im.d, 1.0, im.z, im.d, st));
+    } else {
+      FEDBM_CK(krylov::add_combination(n, jend, im.V, im.hdev, im.d, st));
+    }
     FEDBM_CK(cudaStreamSynchronize(st));  // y (host) is reused by the next cycle
     if (resid <= tol) return FEDBM_OK;
   }
@@ -1699,6 +1741,9 @@ int implicit_step(Batch& b, const fedbm_implicit_params& ip, int nsteps, fedbm_i
   const double eps_mach = g.store == kStoreF64 ? 2.220446049250313e-16 : 1.1920929e-07;
   const double dt = ip.dt;
   const double dtg = dt * tb.A[0][0];
+  if (ip.preconditioner < 0 || ip.preconditioner > 1) return fail(FEDBM_EINVAL, "unknown preconditioner");
+  const bool precond = ip.preconditioner == 1;
+  if (precond && (rc = ensure_block_jacobi(b, g, *im, dtg)) != FEDBM_OK) return rc;
   ImplicitCounters cnt;
   const size_t vb = size_t(n) * sizeof(double);
   for (int step = 0; step < nsteps; ++step) {
@@ -1739,7 +1784,7 @@ int implicit_step(Batch& b, const fedbm_implicit_params& ip, int nsteps, fedbm_i
         double ynorm = 0;
         if ((rc = implicit_norm(b, *im, im->Y, &ynorm)) != FEDBM_OK) return rc;
         const double eps = std::sqrt(eps_mach) * (1.0 + ynorm);
-        if ((rc = implicit_gmres(b, g, *im, dtg, eps, eta * gn, gmax, cnt)) != FEDBM_OK) return rc;
+        if ((rc = implicit_gmres(b, g, *im, dtg, eps, eta * gn, gmax, precond, cnt)) != FEDBM_OK) return rc;
         FEDBM_CK(krylov::axpby(n, 1.0, im->Y, 1.0, im->d, im->Y, st));
       }
       cnt.residual = gn;

@@ -1,6 +1,8 @@
 // Device vector kernels of the implicit solver (see krylov.h).
 #include "krylov.h"
 
+#include <type_traits>
+
 namespace fedbm {
 namespace krylov {
 namespace {
@@ -114,6 +116,132 @@ cudaError_t set_geo_dt(int64_t K, int stride, int slot, double value, void* geo,
   const int grid = grid_of(K);
   if (real_bytes == 8) set_geo_dt_kernel<double><<<grid, kThreads, 0, st>>>(K, stride, slot, value, static_cast<double*>(geo));
   else set_geo_dt_kernel<float><<<grid, kThreads, 0, st>>>(K, stride, slot, value, static_cast<float*>(geo));
+  return cudaGetLastError();
+}
+
+}  // namespace krylov
+}  // namespace fedbm
+
+// ---- element-and-velocity block-Jacobi preconditioner --------------------------
+// For element k and velocity i the block of (I - dtg J) that couples the
+// element's own nodes at velocity i is
+//   M = (1 + dtg / tau_k) I + dtg (a_r Dr + a_s Ds) - dtg LIFT diag(c) E,
+// where a_r = e_x r_x + e_y r_y, a_s = e_x s_x + e_y s_y, E picks the face
+// nodes out of the element's nodes, and c = Fscale (e.n - ab |e.n|) / 2 is the
+// numerical flux's coefficient of the element's own trace on each face (the
+// strong-form residual of eq. byparts).  Neighbour traces, wall reflection and
+// the equilibrium's dependence on the other velocities are left out.  M is
+// inverted by Gauss-Jordan elimination with partial pivoting, one thread per
+// (element, velocity).
+namespace fedbm {
+namespace krylov {
+namespace {
+
+constexpr int kMaxNp = 28;  // degree 6
+
+template <typename R, int NPT>
+__global__ void bj_build_kernel(int64_t K, int Np, int Nfp, int Qp, const R* geo, const double* vel64,
+                                const double* ops, const int* fmask, double dtg, double ab, double* minv) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= K * Qp) return;
+  const int64_t k = t / Qp;
+  const int i = int(t % Qp);
+  const R* g = geo + k * 16;
+  const double ex = vel64[i], ey = vel64[Qp + i];
+  const double ar = ex * double(g[0]) + ey * double(g[2]);
+  const double as = ex * double(g[1]) + ey * double(g[3]);
+  const double itau = double(g[15]);
+  const double* Dr = ops;
+  const double* Ds = ops + Np * Np;
+  const double* LIFT = ops + 2 * Np * Np;
+  const int NF = 3 * Nfp;
+  double A[NPT * NPT], B[NPT * NPT];  // Np <= NPT
+  for (int n = 0; n < Np; ++n)
+    for (int m = 0; m < Np; ++m) {
+      A[n * Np + m] = (n == m ? 1.0 + dtg * itau : 0.0) + dtg * (ar * Dr[n * Np + m] + as * Ds[n * Np + m]);
+      B[n * Np + m] = n == m ? 1.0 : 0.0;
+    }
+  for (int f = 0; f < 3; ++f) {
+    const double en = ex * double(g[4 + 3 * f]) + ey * double(g[5 + 3 * f]);
+    const double c = 0.5 * (en - ab * fabs(en)) * double(g[6 + 3 * f]);
+    if (c == 0.0) continue;
+    for (int a = 0; a < Nfp; ++a) {
+      const int j = f * Nfp + a, m = fmask[j];
+      for (int n = 0; n < Np; ++n) A[n * Np + m] -= dtg * LIFT[n * NF + j] * c;
+    }
+  }
+  // Gauss-Jordan with partial pivoting: B <- A^-1
+  for (int col = 0; col < Np; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < Np; ++r)
+      if (fabs(A[r * Np + col]) > fabs(A[piv * Np + col])) piv = r;
+    if (piv != col)
+      for (int q = 0; q < Np; ++q) {
+        double x = A[col * Np + q]; A[col * Np + q] = A[piv * Np + q]; A[piv * Np + q] = x;
+        x = B[col * Np + q]; B[col * Np + q] = B[piv * Np + q]; B[piv * Np + q] = x;
+      }
+    const double d = 1.0 / A[col * Np + col];
+    for (int q = 0; q < Np; ++q) {
+      A[col * Np + q] *= d;
+      B[col * Np + q] *= d;
+    }
+    for (int r = 0; r < Np; ++r) {
+      if (r == col) continue;
+      const double fct = A[r * Np + col];
+      if (fct == 0.0) continue;
+      for (int q = 0; q < Np; ++q) {
+        A[r * Np + q] -= fct * A[col * Np + q];
+        B[r * Np + q] -= fct * B[col * Np + q];
+      }
+    }
+  }
+  for (int n = 0; n < Np; ++n)
+    for (int m = 0; m < Np; ++m) minv[((k * Np + n) * Np + m) * Qp + i] = B[n * Np + m];
+}
+
+__global__ void bj_apply_kernel(int64_t K, int Np, int Qp, const double* minv, const double* v, double* z) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (t >= K * Qp) return;
+  const int64_t k = t / Qp;
+  const int i = int(t % Qp);
+  double x[kMaxNp];
+  for (int m = 0; m < Np; ++m) x[m] = v[(k * Np + m) * Qp + i];
+  for (int n = 0; n < Np; ++n) {
+    double acc = 0.0;
+    for (int m = 0; m < Np; ++m) acc += minv[((k * Np + n) * Np + m) * Qp + i] * x[m];
+    z[(k * Np + n) * Qp + i] = acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t block_jacobi_build(int64_t K, int Np, int Nfp, int Qp, const void* geo, int real_bytes,
+                               const double* vel64, const double* ops, const int* fmask, double dtg, double ab,
+                               double* minv, cudaStream_t st) {
+  if (Np > kMaxNp) return cudaErrorInvalidValue;
+  const int64_t n = K * Qp;
+  const int blocks = int((n + 127) / 128);
+  // the block size rounded up to a degree's node count keeps the per-thread
+  // work arrays (local memory) small at low degree
+  auto run = [&](auto npt) {
+    constexpr int NPT = decltype(npt)::value;
+    if (real_bytes == 8)
+      bj_build_kernel<double, NPT><<<blocks, 128, 0, st>>>(K, Np, Nfp, Qp, static_cast<const double*>(geo), vel64,
+                                                           ops, fmask, dtg, ab, minv);
+    else
+      bj_build_kernel<float, NPT><<<blocks, 128, 0, st>>>(K, Np, Nfp, Qp, static_cast<const float*>(geo), vel64,
+                                                          ops, fmask, dtg, ab, minv);
+  };
+  if (Np <= 6) run(std::integral_constant<int, 6>{});
+  else if (Np <= 15) run(std::integral_constant<int, 15>{});
+  else run(std::integral_constant<int, kMaxNp>{});
+  return cudaGetLastError();
+}
+
+cudaError_t block_jacobi_apply(int64_t K, int Np, int Qp, const double* minv, const double* v, double* z,
+                               cudaStream_t st) {
+  const int64_t n = K * Qp;
+  bj_apply_kernel<<<int((n + 255) / 256), 256, 0, st>>>(K, Np, Qp, minv, v, z);
   return cudaGetLastError();
 }
 

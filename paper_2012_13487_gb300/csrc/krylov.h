@@ -28,3 +28,21 @@ cudaError_t set_geo_dt(int64_t K, int stride, int slot, double value, void* geo,
 
 }  // namespace krylov
 }  // namespace fedbm
+
+namespace fedbm {
+namespace krylov {
+
+// Element-and-velocity block-Jacobi preconditioner of (I - dtg J) (see
+// krylov.cu): the inverse of every (element, velocity) block, stored
+// [K][Np][Np][Qp], built from the FP64 reference operators ops = [Dr | Ds |
+// LIFT] (row-major, Np*Np, Np*Np, Np*3Nfp), fmask [3][Nfp], the velocity table
+// vel64 [3][Qp] and the element geometry (real_bytes 8 or 4).
+cudaError_t block_jacobi_build(int64_t K, int Np, int Nfp, int Qp, const void* geo, int real_bytes,
+                               const double* vel64, const double* ops, const int* fmask, double dtg, double ab,
+                               double* minv, cudaStream_t st);
+// z = M^-1 v, blockwise
+cudaError_t block_jacobi_apply(int64_t K, int Np, int Qp, const double* minv, const double* v, double* z,
+                               cudaStream_t st);
+
+}  // namespace krylov
+}  // namespace fedbm

@@ -73,7 +73,7 @@ class ImplicitParams(ctypes.Structure):
                 ("b", ctypes.c_double * 6), ("dt", ctypes.c_double), ("newton_rtol", ctypes.c_double),
                 ("newton_atol", ctypes.c_double), ("newton_max_iter", ctypes.c_int32),
                 ("gmres_restart", ctypes.c_int32), ("gmres_max_iter", ctypes.c_int32),
-                ("gmres_rtol", ctypes.c_double)]
+                ("gmres_rtol", ctypes.c_double), ("preconditioner", ctypes.c_int32)]
 
 
 class ImplicitStats(ctypes.Structure):
@@ -299,8 +299,9 @@ def fedbm_rk_stage(h, stage):
 
 
 def implicit_params(scheme=IMPLICIT_BE, dt=1.0, newton_rtol=0.0, newton_atol=0.0, newton_max_iter=0,
-                    gmres_restart=0, gmres_max_iter=0, gmres_rtol=0.0, A=None, b=None):
+                    gmres_restart=0, gmres_max_iter=0, gmres_rtol=0.0, A=None, b=None, preconditioner=0):
     ip = ImplicitParams()
+    ip.preconditioner = preconditioner
     ip.scheme, ip.dt = scheme, dt
     ip.newton_rtol, ip.newton_atol, ip.newton_max_iter = newton_rtol, newton_atol, newton_max_iter
     ip.gmres_restart, ip.gmres_max_iter, ip.gmres_rtol = gmres_restart, gmres_max_iter, gmres_rtol
