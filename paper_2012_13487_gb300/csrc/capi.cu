@@ -401,8 +401,6 @@ struct Group {
   int64_t K = 0;
   std::vector<int> cases;
   int epc = 0, tpb = 0, nstages = 1, grid = 0;
-  int per_sm = 0;       // resident stage CTAs per SM of the configured kernel
-  double tune_us = 0;   // autotuned time of one step-shaped trial (0 = not tuned)
   size_t smem = 0;
   RefOps ops;
   VelocitySet vs;
@@ -542,7 +540,6 @@ int configure_tc(Batch& b, Group& g) {
   g.nstages = 1;
   g.smem = smem;
   g.grid = int(std::min<int64_t>((g.K + g.epc - 1) / g.epc, int64_t(per_sm) * nsm));
-  g.per_sm = per_sm;
   drop_graphs(b);
   return FEDBM_OK;
 }
@@ -568,7 +565,6 @@ int configure_cluster(Batch& b, Group& g, int ncl) {
   g.tpb = 256;
   g.nstages = 1;
   g.smem = smem;
-  g.per_sm = 0;
   g.grid = int(std::min<int64_t>(g.K, int64_t(nclusters_max))) * ncl;
   drop_graphs(b);
   return FEDBM_OK;
@@ -623,7 +619,6 @@ int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
   g.nstages = nst;
   g.smem = smem;
   g.grid = int(std::min<int64_t>(ntiles, int64_t(per_sm) * nsm));
-  g.per_sm = per_sm;
   drop_graphs(b);
   return FEDBM_OK;
 }
@@ -716,7 +711,6 @@ int autotune(Batch& b, const char* cache_path, int trials) {
       if (kv.first == key) hit = &kv.second;
     if (hit && (!hit->tc || tc_available(g)) && (hit->ncl < 2 || cluster_available(g, hit->ncl))) {
       if ((rc = apply_tune(b, g, *hit)) != FEDBM_OK) break;
-      g.tune_us = hit->us;
       continue;
     }
     TuneEntry best;
@@ -778,7 +772,6 @@ int autotune(Batch& b, const char* cache_path, int trials) {
       break;
     }
     if ((rc = apply_tune(b, g, best)) != FEDBM_OK) break;
-    g.tune_us = best.us;
     cache.emplace_back(key, best);
     dirty = true;
   }
