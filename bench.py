@@ -111,7 +111,7 @@ def stage_kernel_sha():
     """Hash of the stage-kernel sources with comments and blank space removed,
     so that only code changes void a recorded ncu traffic figure."""
     h = hashlib.sha256()
-    for n in ("stage_impl.cuh", "stage_tc.cuh", "device_common.cuh"):
+    for n in ("stage_impl.cuh", "stage_tc.cuh", "stage_cluster.cuh", "stage_ws.cuh", "device_common.cuh"):
         with open(os.path.join(ROOT, "paper_2012_13487_gb300", "csrc", n)) as fh:
             code = re.sub(r"//[^\n]*", "", fh.read())
         h.update(" ".join(code.split()).encode())
@@ -548,6 +548,15 @@ def spread(ms, steps):
             "ms_per_step_max": max(per), "spread_pct": 100.0 * (max(per) - min(per)) / statistics.median(per)}
 
 
+def kernel_name(info):
+    """Name of the stage-kernel form a solver's configuration launches."""
+    if info.tensor_cores:
+        return "stage_kernel_tc"
+    if info.velocity_split > 1:
+        return "stage_kernel_cl"
+    return "stage_kernel_ws" if info.pipeline_stages == 3 else "stage_kernel"
+
+
 def roofline_of(dof, prec, ms_per_step, kernel, traffic=None):
     """Roofline of the stage kernel: algorithmic bytes of one launch over the
     average launch time (five launches per step, back to back in a graph)."""
@@ -575,8 +584,7 @@ def measure_form(w, st, steps, warmup, tune, repeats=3):
     info = s.info
     s.mass()
     s.close()
-    kern = "stage_kernel_tc" if info.tensor_cores else ("stage_kernel_cl" if info.velocity_split > 1
-                                                         else "stage_kernel")
+    kern = kernel_name(info)
     return {"value": dof * 5 / (sp["ms_per_step_median"] / 1e3), "unit": "DOF-stage/s", "workload": w["desc"],
             "precision": w["precision"], "reduction": w.get("reduction", "default"), "dof": dof,
             "steps": steps, "repeats": sp,
@@ -623,7 +631,7 @@ def run_ours(args, w, name):
     ms_step = sp["ms_per_step_median"]
     secs = ms_step * args.steps / 1e3
     value = job_throughput(world, dof * 5 * args.steps, secs)
-    kern = ("stage_kernel_tc" if s.info.tensor_cores else "stage_kernel") + " (5 launches per step; average over the mix)"
+    kern = kernel_name(s.info) + " (5 launches per step; average over the mix)"
     roof = roofline_of(dof, w["precision"], ms_step, kern, recorded_traffic(name))
 
     # end to end through the C ABI with host buffers

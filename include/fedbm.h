@@ -138,7 +138,14 @@ typedef struct fedbm_params {
   int32_t threads_per_cta; /* stage-kernel tile: threads per CTA, multiple of 32,
                             <= 256 (0 = auto)                                  */
   int32_t pipeline_stages; /* stage-kernel tile buffers per CTA: 1, or 2 to load
-                              the next tile while computing one (0 = auto = 1) */
+                              the next tile while computing one (0 = auto = 1);
+                              3 = the warp-specialised form: a producer warp
+                              keeps a ring of three one-element tiles filled
+                              (bulk copies) for eight consumer warps, one
+                              velocity per thread, 288 threads per CTA (tile
+                              arguments ignored); FP32 or BF16 state with 256
+                              padded velocities at degree <= 5, else EINVAL.
+                              The autotuner times it where it exists      */
   int32_t tensor_cores;  /* stage-kernel form: 0 = the FMA kernel (the
                             faster form on every measured shape), with the
                             tensor-core form as one of the autotuner's
@@ -178,7 +185,8 @@ typedef struct fedbm_info_t {
   int64_t steps;                 /* completed RK steps                           */
   int32_t precision, reduction, order, eq_order;
   int32_t elems_per_cta, threads_per_cta;
-  int32_t pipeline_stages, grid; /* stage-kernel buffers per CTA; persistent grid */
+  int32_t pipeline_stages, grid; /* stage-kernel buffers per CTA (3: the warp-
+                                    specialised form); persistent grid          */
   int32_t group, ngroups;        /* batches: kernel group of this case; group count */
   int32_t tensor_cores;          /* 1 if the group's stage kernel is the tensor-core form */
   int32_t velocity_split;        /* CTAs per element tile: 1, or the cluster size of the
@@ -379,7 +387,8 @@ int fedbm_batch_info(const fedbm_batch* b, int32_t c, fedbm_info_t* info);
 /* Advance every case nsteps LSRK(5,4) steps (one graph launch per step). */
 int fedbm_batch_rk_step(fedbm_batch* b, int32_t nsteps);
 /* Re-tile one group's stage kernel as the FMA form (0 = automatic for each
- * argument); used by the tile autotuner.  Takes effect from the next step.
+ * argument; pipeline_stages = 3 selects the warp-specialised form, whose tile
+ * is fixed); used by the tile autotuner.  Takes effect from the next step.
  * On EINVAL (a tile that is not valid or does not fit shared memory) the group
  * keeps its current form and tile. */
 int fedbm_batch_set_tiles(fedbm_batch* b, int32_t group, int32_t elems_per_cta,

@@ -489,6 +489,7 @@ cudaError_t launch_args(const Group& g, const void* args, cudaStream_t st, int g
   if (grid <= 0) grid = g.grid;
   if (g.ncl > 1) return e.launch_cl(g.store, args, g.grid / g.ncl, g.ncl, g.smem, st);
   if (g.tc) return e.launch_tc(g.store, args, grid, g.smem, st);
+  if (g.nstages == 3) return e.launch_ws(g.store, args, grid, g.smem, st);
   return e.launch(g.store, args, grid, g.tpb, g.smem, st);
 }
 
@@ -589,13 +590,41 @@ int auto_cluster(const Group& g) {
   return best;
 }
 
+// The warp-specialised form of a group: one element per ring stage, eight
+// consumer warps (one velocity per thread) and one producer warp.
+bool ws_available(const Group& g) { return stage_entry(g.p).ws_smem(g.store, g.Qp) > 0; }
+
+int configure_ws(Batch& b, Group& g) {
+  const StageEntry e = stage_entry(g.p);
+  const size_t smem = e.ws_smem(g.store, g.Qp);
+  if (smem == 0)
+    return fail(FEDBM_EINVAL, "pipeline_stages = 3 (the warp-specialised stage kernel) needs FP32 or BF16 state, "
+                              "256 padded velocities and degree <= 5");
+  if (smem > kMaxSmem) return fail(FEDBM_EINVAL, "warp-specialised ring does not fit in shared memory");
+  FEDBM_CK(e.set_smem_ws(g.store, kMaxSmem));
+  int nsm = 0;
+  FEDBM_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b.device));
+  const int per_sm = e.occupancy_ws(g.store, smem);
+  if (per_sm < 1) return fail(FEDBM_EINVAL, "warp-specialised stage kernel cannot be resident on an SM");
+  g.tc = 0;
+  g.ncl = 0;
+  g.epc = 1;
+  g.tpb = 288;
+  g.nstages = 3;
+  g.smem = smem;
+  g.grid = int(std::min<int64_t>(g.K, int64_t(per_sm) * nsm));
+  drop_graphs(b);
+  return FEDBM_OK;
+}
+
 // Tile shape, pipeline depth and persistent grid of a group's stage kernel.
 int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
+  if (stages == 3) return configure_ws(b, g);  // tile and threads are the form's own
   // the group is changed only once the whole configuration is valid
   const int e_pc = epc > 0 ? epc : (g.Qp < 128 ? std::max(1, 128 / g.Qp) : 1);
   const int t_pb = tpb > 0 ? tpb : std::min(128, std::max(32, (e_pc * g.Qp + 31) / 32 * 32));
   if (t_pb % 32 || t_pb > 256) return fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256");
-  if (stages < 0 || stages > 2) return fail(FEDBM_EINVAL, "pipeline_stages must be 0, 1 or 2");
+  if (stages < 0 || stages > 3) return fail(FEDBM_EINVAL, "pipeline_stages must be 0, 1, 2 or 3");
   int nst = stages == 2 ? 2 : 1;
   size_t smem = stage_smem_bytes(g.p, g.store, e_pc, g.Qp, nst);
   if (smem > kMaxSmem && nst == 2) {
@@ -709,7 +738,8 @@ int autotune(Batch& b, const char* cache_path, int trials) {
     const TuneEntry* hit = nullptr;
     for (auto& kv : cache)
       if (kv.first == key) hit = &kv.second;
-    if (hit && (!hit->tc || tc_available(g)) && (hit->ncl < 2 || cluster_available(g, hit->ncl))) {
+    if (hit && (!hit->tc || tc_available(g)) && (hit->ncl < 2 || cluster_available(g, hit->ncl)) &&
+        (hit->stages != 3 || ws_available(g))) {
       if ((rc = apply_tune(b, g, *hit)) != FEDBM_OK) break;
       continue;
     }
@@ -746,6 +776,13 @@ int autotune(Batch& b, const char* cache_path, int trials) {
           time_current(cand);
         }
       }
+    }
+    if (ws_available(g) && configure_ws(b, g) == FEDBM_OK) {
+      TuneEntry cand;
+      cand.epc = 1;
+      cand.tpb = 288;
+      cand.stages = 3;
+      time_current(cand);
     }
     if (tc_available(g) && configure_tc(b, g) == FEDBM_OK) {
       TuneEntry cand;

@@ -24,6 +24,13 @@ struct StageEntry {
   cudaError_t (*launch_cl)(int store_kind, const void* args, int nclusters, int ncl, size_t smem, cudaStream_t st);
   cudaError_t (*set_smem_cl)(int store_kind, size_t smem);
   int (*occupancy_cl)(int store_kind, int ncl, size_t smem);  // resident clusters on the device
+  // warp-specialised form (a producer warp filling a three-stage ring of
+  // element tiles for eight consumer warps; FP32 or BF16 state, 256 padded
+  // velocities, degree <= 5)
+  size_t (*ws_smem)(int store_kind, int Qp);  // 0 = no such form
+  cudaError_t (*launch_ws)(int store_kind, const void* args, int grid, size_t smem, cudaStream_t st);
+  cudaError_t (*set_smem_ws)(int store_kind, size_t smem);
+  int (*occupancy_ws)(int store_kind, size_t smem);  // resident CTAs per SM
 };
 
 StageEntry stage_entry_p0();

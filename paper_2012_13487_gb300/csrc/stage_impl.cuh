@@ -874,6 +874,7 @@ __global__ void __launch_bounds__(256, stage_min_blocks<ST, QT>()) stage_kernel(
 
 #include "stage_tc.cuh"
 #include "stage_cluster.cuh"
+#include "stage_ws.cuh"
 
 template <class ST, int QT>
 cudaError_t launch_one(const void* args, int grid, int block, size_t smem, cudaStream_t st) {
@@ -1007,6 +1008,10 @@ StageEntry FEDBM_STAGE_ENTRY_NAME() {
   s.launch_cl = &launch_cl;
   s.set_smem_cl = &set_smem_cl;
   s.occupancy_cl = &occupancy_cl;
+  s.ws_smem = &ws_smem;
+  s.launch_ws = &launch_ws;
+  s.set_smem_ws = &set_smem_ws;
+  s.occupancy_ws = &occupancy_ws;
   return s;
 }
 
