@@ -138,7 +138,11 @@ typedef struct fedbm_params {
   int32_t threads_per_cta; /* stage-kernel tile: threads per CTA, multiple of 32,
                             <= 256 (0 = auto)                                  */
   int32_t pipeline_stages; /* stage-kernel tile buffers per CTA: 1, or 2 to load
-                              the next tile while computing one (0 = auto = 1);
+                              the next tile while computing one (0 = auto: 3
+                              where that form measured faster, i.e. 256 padded
+                              velocities with FP32 state at degree 1-4 or BF16
+                              at degree 3-5, when the tile arguments are 0
+                              too; else 1);
                               3 = the warp-specialised form: a producer warp
                               keeps a ring of three one-element tiles filled
                               (bulk copies) for eight consumer warps, one
@@ -395,7 +399,9 @@ int fedbm_batch_set_tiles(fedbm_batch* b, int32_t group, int32_t elems_per_cta,
                           int32_t threads_per_cta, int32_t pipeline_stages);
 /* Switch one group's stage kernel to the tensor-core form (on = 1; EINVAL if
  * the group's form has none, or if it was created with tensor_cores = -1) or
- * back to the FMA form with automatic tiles (on = 0).  Next step onwards. */
+ * back to the default FMA form with automatic tiles (on = 0; the
+ * warp-specialised form where pipeline_stages = 0 would choose it).  Next step
+ * onwards. */
 int fedbm_batch_set_tensor_cores(fedbm_batch* b, int32_t group, int32_t on);
 
 /* Tile autotuner: for every kernel group, time each candidate stage-kernel

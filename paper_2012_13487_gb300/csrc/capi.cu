@@ -594,6 +594,17 @@ int auto_cluster(const Group& g) {
 // consumer warps (one velocity per thread) and one producer warp.
 bool ws_available(const Group& g) { return stage_entry(g.p).ws_smem(g.store, g.Qp) > 0; }
 
+// The untuned default takes the warp-specialised form where it measured
+// faster than the FMA kernel's default tile on the 256-velocity cavities of
+// about 30M DOF: FP32 state at degree 1-4 (x1.04-1.12), BF16 at degree 3-5
+// (x1.21-1.41, the volume contractions on tensor cores).  FP32 at degree 5
+// holds one CTA per SM (three 39 KB stages) and BF16 at degree 1-2 loses to
+// the FMA kernel's two velocities per thread.
+bool ws_default(const Group& g) {
+  if (!ws_available(g)) return false;
+  return (g.store == kStoreF32 && g.p >= 1 && g.p <= 4) || (g.store == kStoreBF16 && g.p >= 3);
+}
+
 int configure_ws(Batch& b, Group& g) {
   const StageEntry e = stage_entry(g.p);
   const size_t smem = e.ws_smem(g.store, g.Qp);
@@ -1104,12 +1115,13 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
          for (Group& g : b->groups) {
            const int epc = g.epc, tpb = g.tpb, st = g.nstages;
            if ((r = build_group(*b, g)) != FEDBM_OK) return r;
-           // default: the FMA kernel for every form (with its compile-time
-           // operator tables it measured faster than the tensor-core form on
-           // FP32 state too, 2.52e11 vs 2.04e11-2.20e11 DOF-stage/s at 256
-           // velocities; the 16-bit forms, 1024 velocities, stacked 16-velocity
-           // tiles and degree 5 likewise); tensor cores on request
-           // (tensor_cores = 1) or when the autotuner times them faster
+           // default: the FMA kernel for every form, as its warp-specialised
+           // variant where ws_default says so (with its compile-time operator
+           // tables it measured faster than the tensor-core form on FP32 state
+           // too, 2.52e11 vs 2.04e11-2.20e11 DOF-stage/s at 256 velocities;
+           // the 16-bit forms, 1024 velocities, stacked 16-velocity tiles and
+           // degree 5 likewise); tensor cores on request (tensor_cores = 1) or
+           // when the autotuner times them faster
            const bool want_tc = g.tc_mode > 0;
            // the velocity-split form on request, or when one CTA cannot hold
            // an element's velocities (automatic mode)
@@ -1119,6 +1131,8 @@ int create_batch(const fedbm_case_desc* cd, int ncases, void* stream, Batch** ou
              if ((r = configure_cluster(*b, g, ncl)) != FEDBM_OK) return r;
            } else if (want_tc) {
              if ((r = configure_tc(*b, g)) != FEDBM_OK) return r;
+           } else if (epc == 0 && tpb == 0 && st == 0 && g.vsplit <= 1 && ws_default(g)) {
+             if ((r = configure_ws(*b, g)) != FEDBM_OK) return r;
            } else if ((r = configure_tiles(*b, g, epc, tpb, st)) != FEDBM_OK) {
              return r;
            }
@@ -2106,7 +2120,9 @@ extern "C" int fedbm_batch_set_tiles(fedbm_batch* h, int32_t group, int32_t elem
 extern "C" int fedbm_batch_set_tensor_cores(fedbm_batch* h, int32_t group, int32_t on) {
   FEDBM_BATCH(h, 0);
   if (group < 0 || group >= int(B.groups.size())) return fail(FEDBM_EINVAL, "group index out of range");
-  return on ? configure_tc(B, B.groups[group]) : configure_tiles(B, B.groups[group], 0, 0, 0);
+  Group& g = B.groups[group];
+  if (on) return configure_tc(B, g);
+  return ws_default(g) && g.vsplit <= 1 ? configure_ws(B, g) : configure_tiles(B, g, 0, 0, 0);
 }
 
 extern "C" int fedbm_batch_autotune(fedbm_batch* h, const char* cache_path, int32_t trials) {

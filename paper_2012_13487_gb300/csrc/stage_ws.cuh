@@ -293,22 +293,52 @@ __global__ void __launch_bounds__(kWsThreads, 2) stage_kernel_ws(const StageArgs
     const int* nb = st_nbr(s);
     float* mom = reinterpret_cast<float*>(smem + o.mom) + (j & 1) * NP * 8;
     float* wn = reinterpret_cast<float*>(smem + o.wn) + (j & 1) * NF;
+    const float sc = ST::dev ? st_scale(s)[0] : 0.f;
+    const float ws = ST::dev ? w * sc : 0.f;
+    float fr[NP];  // this velocity's state at the element's nodes
     if constexpr (kMma) {
-      // this velocity's q column as row i of the MMA operand (K-major; the
-      // previous element's MMAs have completed, so the operand is free)
+      // this velocity's q column, once: row i of the MMA operand (K-major; the
+      // previous element's MMAs have completed, so the operand is free), and
+      // decoded
+      uint32_t qb[MK];
 #pragma unroll
-      for (int c = 0; c < MKC; ++c) {
-        uint32_t wv[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int k0 = 8 * c + 2 * t;
-          const uint32_t lo = k0 < NP ? uint32_t(__bfloat16_as_ushort(sf[k0 * kWsQ + i])) : 0u;
-          const uint32_t hi = k0 + 1 < NP ? uint32_t(__bfloat16_as_ushort(sf[(k0 + 1) * kWsQ + i])) : 0u;
-          wv[t] = lo | (hi << 16);
+      for (int m = 0; m < MK; ++m) {
+        if (m < NP) {
+          const S q = sf[m * kWsQ + i];
+          qb[m] = uint32_t(__bfloat16_as_ushort(q));
+          fr[m] = decode<ST>(q, w, ws);
+        } else {
+          qb[m] = 0u;
         }
-        *reinterpret_cast<uint4*>(sA + bidx(i, 8 * c, MKC)) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
       }
+#pragma unroll
+      for (int c = 0; c < MKC; ++c)
+        *reinterpret_cast<uint4*>(sA + bidx(i, 8 * c, MKC)) =
+            make_uint4(qb[8 * c] | (qb[8 * c + 1] << 16), qb[8 * c + 2] | (qb[8 * c + 3] << 16),
+                       qb[8 * c + 4] | (qb[8 * c + 5] << 16), qb[8 * c + 6] | (qb[8 * c + 7] << 16));
     }
+
+    // one thread issues the element's MMAs: D[h] = q[h] [Dr; Ds]^T summed over
+    // the operator pieces, h = velocities 128 h .. 128 h + 127
+    auto issue_mma = [&]() {
+      if (tid == 0) {
+        tc::fence_after_sync();
+        const uint64_t dA = tc::sdesc(smem_u32(sA), 128, MKC * 128), dB = tc::sdesc(smem_u32(sB), 128, MKC * 128);
+        constexpr uint32_t id = idesc_bf16(128, MN);
+        const uint32_t tm = *tslot;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int ks = 0; ks < MK / 16; ++ks)
+#pragma unroll
+            for (int q = 0; q < kPieces; ++q) {
+              const uint64_t ao = uint64_t(h * 16 * MKC * 128 + ks * 256) >> 4;
+              const uint64_t bo = uint64_t(q * MN * MK * 2 + ks * 256) >> 4;
+              mma_bf16(tm + uint32_t(h * MN), dA + ao, dB + bo, id, (ks | q) != 0);
+            }
+        tc::mma_commit(mma_bar);
+      }
+    };
 
     // ---- node moments (as in the FMA kernel) and wall numerators -----------
     if (!a.collision) {
@@ -320,7 +350,6 @@ __global__ void __launch_bounds__(kWsThreads, 2) stage_kernel_ws(const StageArgs
     } else {
       tile_moments<ST, AccF, kWsQ, kWsConsumers, 1>(a, sf, st_scale(s), g, mom, 1, s_vel);
     }
-    const float sc = ST::dev ? st_scale(s)[0] : 0.f;
     if (a.wall_any) {
       // one warp per wall face node: sum over outgoing velocities of (e.n) f^-
       const int lane = tid & 31, warp = tid >> 5;
@@ -345,34 +374,17 @@ __global__ void __launch_bounds__(kWsThreads, 2) stage_kernel_ws(const StageArgs
       tc::fence_before_sync();
     }
     consumers_sync();
-    if constexpr (kMma) {
-      if (tid == 0) {
-        // D[h] = q[h] [Dr; Ds]^T over the pieces, h = velocities 128 h ..
-        tc::fence_after_sync();
-        const uint64_t dA = tc::sdesc(smem_u32(sA), 128, MKC * 128), dB = tc::sdesc(smem_u32(sB), 128, MKC * 128);
-        constexpr uint32_t id = idesc_bf16(128, MN);
-        const uint32_t tm = *tslot;
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int ks = 0; ks < MK / 16; ++ks)
-#pragma unroll
-            for (int q = 0; q < kPieces; ++q) {
-              const uint64_t ao = uint64_t(h * 16 * MKC * 128 + ks * 256) >> 4;
-              const uint64_t bo = uint64_t(q * MN * MK * 2 + ks * 256) >> 4;
-              mma_bf16(tm + uint32_t(h * MN), dA + ao, dB + bo, id, (ks | q) != 0);
-            }
-        tc::mma_commit(mma_bar);
-      }
-    }
+    // the MMAs run while the fluxes and the lift contraction are computed
+    if constexpr (kMma) issue_mma();
+
 
     // ---- residual and update of velocity i, all nodes ---------------------
     const float dt = g[kGeoDt], inv_tau = g[kGeoInvTau];
     const float ar = ex * g[0] + ey * g[2], as = ex * g[1] + ey * g[3];
-    const float ws = ST::dev ? w * sc : 0.f;
-    float fr[NP];
+    if constexpr (!kMma) {
 #pragma unroll
-    for (int m = 0; m < NP; ++m) fr[m] = decode<ST>(sf[m * kWsQ + i], w, ws);
+      for (int m = 0; m < NP; ++m) fr[m] = decode<ST>(sf[m * kWsQ + i], w, ws);
+    }
     float flux[NF];
 #pragma unroll
     for (int fc = 0; fc < 3; ++fc) {
@@ -433,8 +445,9 @@ __global__ void __launch_bounds__(kWsThreads, 2) stage_kernel_ws(const StageArgs
       if (!mbar_wait_bounded(mma_bar, uint32_t(j & 1), 2000000000ull) && a.err) atomicExch(a.err, 1);
       __syncwarp();
       tc::fence_after_sync();
+      constexpr int NG = (NP + 7) / 8;
 #pragma unroll
-      for (int c = 0; c < (NP + 7) / 8; ++c) {
+      for (int c = 0; c < NG; ++c) {
         float V[8], W[8];
         tc::tmem_ld8(ta + 8 * c, V);
         tc::tmem_ld8(ta + MND + 8 * c, W);
@@ -521,8 +534,11 @@ int occupancy_ws_as(size_t smem) {
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
     cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
-    const int by_regs = regs_sm / (regs_warp * (ws::kWsThreads / 32));
+    // registers are allocated per warp in units of 256, from the register file
+    // of the warp's SM sub-partition (a quarter of the SM's): count warps per
+    // sub-partition, then CTAs of nine warps
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = 4 * ((regs_sm / 4) / regs_warp) / (ws::kWsThreads / 32);
     const int by_smem = int(size_t(smem_sm) / (smem + fa.sharedSizeBytes + size_t(reserved)));
     const int by_thr = thr_sm / ws::kWsThreads;
     const int by_tmem = ws::ws_mma<ST>() ? 512 / ws::kMmaCols : by_thr;
