@@ -118,16 +118,23 @@ def stage_kernel_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(name):
+def recorded_traffic(name, kernel, precision=None):
     """DRAM bytes per stage launch from the committed ncu summary, if it was
-    taken for the current kernel source; else None."""
+    taken for the current kernel source, the kernel form and the state
+    precision this run times; else None."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_%s.md" % name)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m1 = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m3 = re.search(r"^kernel:\s*(\S+)", txt, re.M)
     if not m1 or not m2 or m1.group(1) != stage_kernel_sha():
+        return None
+    if m3 and m3.group(1) != kernel:
+        return None
+    m4 = re.search(r"^precision:\s*(\S+)", txt, re.M)
+    if precision and m4 and m4.group(1) != precision:
         return None
     return float(m2.group(1))
 
@@ -569,7 +576,7 @@ def roofline_of(dof, prec, ms_per_step, kernel, traffic=None):
             "algorithmic_bytes_per_launch": alg / 5.0, "kernel": kernel}
 
 
-def measure_form(w, st, steps, warmup, tune, repeats=3):
+def measure_form(w, st, steps, warmup, tune, repeats=3, profile=None):
     """Throughput of one (workload, precision, reduction) form: the FMA kernel
     by default, autotuned over both kernel forms when `tune`."""
     s = make_solver(w, st.cuda_stream)
@@ -591,7 +598,8 @@ def measure_form(w, st, steps, warmup, tune, repeats=3):
             "tile": {"elems_per_cta": info.elems_per_cta, "threads_per_cta": info.threads_per_cta,
                      "pipeline_stages": info.pipeline_stages, "grid": info.grid,
                      "tensor_cores": info.tensor_cores, "velocity_split": info.velocity_split},
-            "roofline": roofline_of(dof, w["precision"], sp["ms_per_step_median"], kern)}
+            "roofline": roofline_of(dof, w["precision"], sp["ms_per_step_median"], kern,
+                                    recorded_traffic(profile, kern, w["precision"]) if profile else None)}
 
 
 def run_ours(args, w, name):
@@ -632,7 +640,8 @@ def run_ours(args, w, name):
     secs = ms_step * args.steps / 1e3
     value = job_throughput(world, dof * 5 * args.steps, secs)
     kern = kernel_name(s.info) + " (5 launches per step; average over the mix)"
-    roof = roofline_of(dof, w["precision"], ms_step, kern, recorded_traffic(name))
+    roof = roofline_of(dof, w["precision"], ms_step, kern,
+                       recorded_traffic(name, kernel_name(s.info), w["precision"]))
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(3, min(args.steps, 20))
@@ -787,6 +796,15 @@ FORMS = [
 ]
 
 
+# the committed ncu summary (by workload name) whose traffic a form reports
+FORM_PROFILES = {
+    "bf16_state": "cavity_kn1_64x64x2_p4_nc16x16_bf16",
+    "couette_256x256x2_p5_gh16_fp32": "couette_kn1_256x256x2_p5_gh16_fp32",
+    "cavity_kn8_128x128x2_p3_nc32_bf16_red_comp": "cavity_kn8_128x128x2_p3_nc32x32_bf16",
+    "cavity_kn8_32x32x2_p5_d2q1089_fp32_split": "cavity_kn8_32x32x2_p5_nc33x33_sqrt2_fp32",
+}
+
+
 def measure_forms(args, w, st, value, roof, error):
     """Every form of FORMS (throughput, roofline, error on its copy) and the
     seeded 256-case batch against a loop of single solvers."""
@@ -801,7 +819,7 @@ def measure_forms(args, w, st, value, roof, error):
         base = WORKLOADS[wname]["desc"].split(", BF16")[0].split(", FP32")[0]
         wf["desc"] = "%s [%s state, %s moment sums%s]" % (base, prec.upper(), red,
                                                          ", stochastic rounding" if wf.get("rounding") else "")
-        forms[key] = measure_form(wf, st, steps, args.warmup, not args.no_tune)
+        forms[key] = measure_form(wf, st, steps, args.warmup, not args.no_tune, profile=FORM_PROFILES.get(key))
         by_copy.setdefault(wname, []).append((key, prec, red, wf.get("rounding", 0)))
     if not args.no_error:
         for wname, items in by_copy.items():
