@@ -632,8 +632,16 @@ int configure_ws(Batch& b, Group& g) {
 int configure_tiles(Batch& b, Group& g, int epc, int tpb, int stages) {
   if (stages == 3) return configure_ws(b, g);  // tile and threads are the form's own
   // the group is changed only once the whole configuration is valid
-  const int e_pc = epc > 0 ? epc : (g.Qp < 128 ? std::max(1, 128 / g.Qp) : 1);
-  const int t_pb = tpb > 0 ? tpb : std::min(128, std::max(32, (e_pc * g.Qp + 31) / 32 * 32));
+  int e_pc = epc > 0 ? epc : (g.Qp < 128 ? std::max(1, 128 / g.Qp) : 1);
+  int t_pb = tpb > 0 ? tpb : std::min(128, std::max(32, (e_pc * g.Qp + 31) / 32 * 32));
+  if (epc == 0 && tpb == 0 && g.Qp == 16 && (g.store == kStoreF32 || g.store == kStoreBF16)) {
+    // 16 velocities: the autotuner's picks on ~20-45M-DOF Couette cases (FP32
+    // x1.4 at degree 1, x1.15 at 2; BF16 x1.9, 1.8, 1.6, 1.25, 1.04 at 1..5):
+    // 16 elements per tile up to degree 2, else 8; 64 threads for BF16 state
+    // (one item per thread where two velocities share a thread)
+    e_pc = g.p <= 2 ? 16 : 8;
+    t_pb = g.store == kStoreBF16 ? 64 : 128;
+  }
   if (t_pb % 32 || t_pb > 256) return fail(FEDBM_EINVAL, "threads_per_cta must be a multiple of 32, <= 256");
   if (stages < 0 || stages > 3) return fail(FEDBM_EINVAL, "pipeline_stages must be 0, 1, 2 or 3");
   int nst = stages == 2 ? 2 : 1;
