@@ -36,6 +36,10 @@ namespace ws {
 #ifndef FEDBM_WS_MMA
 #define FEDBM_WS_MMA 1
 #endif
+// FEDBM_WS_SKIP = 0 evaluates every face's flux and lift columns
+#ifndef FEDBM_WS_SKIP
+#define FEDBM_WS_SKIP 1
+#endif
 constexpr int kWsStages = 3;
 constexpr int kWsQ = 256;                  // velocities (one per consumer thread)
 constexpr int kWsConsumers = kWsQ;         // eight warps
@@ -386,11 +390,19 @@ __global__ void __launch_bounds__(kWsThreads, 2) stage_kernel_ws(const StageArgs
       for (int m = 0; m < NP; ++m) fr[m] = decode<ST>(sf[m * kWsQ + i], w, ws);
     }
     float flux[NF];
+    // face fc carries flux for some velocity of this warp (warp-uniform; with
+    // the upwind flux an outflow face's jump term is zero, so a face that is
+    // outflow for all 32 velocities skips its traces and lift columns)
+    bool on[3];
 #pragma unroll
     for (int fc = 0; fc < 3; ++fc) {
       const float en = ex * g[4 + 3 * fc] + ey * g[5 + 3 * fc];
       const float c = 0.5f * (en - ab * fabsf(en)) * g[6 + 3 * fc];
       const int code = nb[fc];
+      on[fc] = FEDBM_WS_SKIP ? __any_sync(kFull, c != 0.f && (code >= 0 || en < 0.f)) : true;
+#pragma unroll
+      for (int aa = 0; aa < NFP; ++aa) flux[fc * NFP + aa] = 0.f;
+      if (!on[fc]) continue;
       if (code >= 0) {
         const float wsn = ST::dev ? w * st_nscale(s)[fc] : 0.f;
         const S* trow = st_tr(s) + fc * NFP * kWsQ + i;
@@ -436,10 +448,17 @@ __global__ void __launch_bounds__(kWsThreads, 2) stage_kernel_ws(const StageArgs
       // lift on FMAs while the MMAs run, then the accumulators in groups of 8 nodes
       float lf[NP];
 #pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        lf[n] = 0.f;
+      for (int n = 0; n < NP; ++n) lf[n] = 0.f;
 #pragma unroll
-        for (int q = 0; q < NF; ++q) lf[n] = fmaf(opv<float, kImm>(OFF_LIFT + n * NF + q), flux[q], lf[n]);
+      for (int fc = 0; fc < 3; ++fc) {
+        if (!on[fc]) continue;
+#pragma unroll
+        for (int n = 0; n < NP; ++n)
+#pragma unroll
+          for (int aa = 0; aa < NFP; ++aa) {
+            const int q = fc * NFP + aa;
+            lf[n] = fmaf(opv<float, kImm>(OFF_LIFT + n * NF + q), flux[q], lf[n]);
+          }
       }
       const float arw = ar * ws, asw = as * ws;  // Dr f = w s (Dr q)
       if (!mbar_wait_bounded(mma_bar, uint32_t(j & 1), 2000000000ull) && a.err) atomicExch(a.err, 1);
@@ -455,6 +474,32 @@ __global__ void __launch_bounds__(kWsThreads, 2) stage_kernel_ws(const StageArgs
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           if (8 * c + q < NP) finish(8 * c + q, fmaf(-arw, V[q], fmaf(-asw, W[q], lf[8 * c + q])));
+      }
+    } else if (FEDBM_WS_SKIP) {
+      // lift by faces (the faces without flux skipped), then volume and update
+      float lf[NP];
+#pragma unroll
+      for (int n = 0; n < NP; ++n) lf[n] = 0.f;
+#pragma unroll
+      for (int fc = 0; fc < 3; ++fc) {
+        if (!on[fc]) continue;
+#pragma unroll
+        for (int n = 0; n < NP; ++n)
+#pragma unroll
+          for (int aa = 0; aa < NFP; ++aa) {
+            const int q = fc * NFP + aa;
+            lf[n] = fmaf(opv<float, kImm>(OFF_LIFT + n * NF + q), flux[q], lf[n]);
+          }
+      }
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        float dr = 0.f, ds = 0.f;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          dr = fmaf(opv<float, kImm>(OFF_DR + n * NP + m), fr[m], dr);
+          ds = fmaf(opv<float, kImm>(OFF_DS + n * NP + m), fr[m], ds);
+        }
+        finish(n, fmaf(-ar, dr, fmaf(-as, ds, lf[n])));
       }
     } else {
 #pragma unroll
