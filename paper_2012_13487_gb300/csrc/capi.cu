@@ -101,13 +101,15 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 // canonical f = f^eq(rho0, u0) (1 + amp u(seed, index)) in FP64
-__global__ void equilibrium_kernel(double* out, const double* vel64, int64_t K, int Np, int Q, int Qp,
-                                   double rho0, double ux0, double uy0, double amp, uint64_t seed,
+// (vel64 in the internal velocity order, iperm[c] = internal index of
+// canonical velocity c)
+__global__ void equilibrium_kernel(double* out, const double* vel64, const int32_t* iperm, int64_t K, int Np,
+                                   int Q, int Qp, double rho0, double ux0, double uy0, double amp, uint64_t seed,
                                    int eq_order) {
   const int64_t n = K * Np * Q;
   for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < n;
        idx += int64_t(gridDim.x) * blockDim.x) {
-    const int i = int(idx % Q);
+    const int i = iperm[int(idx % Q)];
     const double ex = vel64[i], ey = vel64[Qp + i], w = vel64[2 * Qp + i];
     const double eu = ex * ux0 + ey * uy0, uu = ux0 * ux0 + uy0 * uy0;
     double poly = 1.0 + eu + 0.5 * (eu * eu - uu);
@@ -119,11 +121,12 @@ __global__ void equilibrium_kernel(double* out, const double* vel64, int64_t K, 
   }
 }
 
-// canonical FP64 or FP32 [K][Np][Q] -> internal storage [K][Np][Qp] (one CTA
+// canonical FP64 or FP32 [K][Np][Q] -> internal storage [K][Np][Qp], canonical
+// velocity c at internal index iperm[c], the padding velocities zero (one CTA
 // per element; the deviation forms compute their scale and codes in FP64)
 template <class ST, typename TIn>
-__global__ void encode_kernel(const TIn* in, void* out, float* scale, const double* vel64, int Np, int Q,
-                              int Qp) {
+__global__ void encode_kernel(const TIn* in, void* out, float* scale, const double* vel64, const int32_t* iperm,
+                              int Np, int Q, int Qp) {
   using S = typename ST::S;
   const int64_t k = blockIdx.x;
   const TIn* src = in + k * Np * Q;
@@ -133,7 +136,7 @@ __global__ void encode_kernel(const TIn* in, void* out, float* scale, const doub
     __shared__ float red[32];
     float m = 0.f;
     for (int j = threadIdx.x; j < Np * Q; j += blockDim.x) {
-      const int i = j % Q;
+      const int i = iperm[j % Q];
       if (w[i] > 0) m = fmaxf(m, float(fabs((double(src[j]) - w[i]) / w[i])));
     }
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -153,20 +156,19 @@ __global__ void encode_kernel(const TIn* in, void* out, float* scale, const doub
     }
     __syncthreads();
     const double inv_s = 1.0 / double(red[0]);
-    for (int j = threadIdx.x; j < Np * Qp; j += blockDim.x) {
-      const int n = j / Qp, i = j % Qp;
+    for (int j = threadIdx.x; j < Np * Q; j += blockDim.x) {
+      const int n = j / Q, i = iperm[j % Q];
       float q = 0.f;
-      if (i < Q && w[i] > 0) q = float((double(src[n * Q + i]) - w[i]) / w[i] * inv_s);
-      dst[j] = ST::from_r(q);
+      if (w[i] > 0) q = float((double(src[j]) - w[i]) / w[i] * inv_s);
+      dst[n * Qp + i] = ST::from_r(q);
     }
   } else {
     (void)scale;
     (void)w;
-    for (int j = threadIdx.x; j < Np * Qp; j += blockDim.x) {
-      const int n = j / Qp, i = j % Qp;
-      dst[j] = S(i < Q ? double(src[n * Q + i]) : 0.0);
-    }
+    for (int j = threadIdx.x; j < Np * Q; j += blockDim.x) dst[(j / Q) * Qp + iperm[j % Q]] = S(double(src[j]));
   }
+  for (int j = threadIdx.x; j < Np * (Qp - Q); j += blockDim.x)
+    dst[(j / (Qp - Q)) * Qp + Q + j % (Qp - Q)] = S(0.0f);
 }
 
 template <class ST>
@@ -175,16 +177,16 @@ __device__ __forceinline__ double decode64(const typename ST::S v, double w, dou
   else return double(v);
 }
 
-// internal state -> canonical FP64
+// internal state -> canonical FP64 (canonical velocity c from internal index iperm[c])
 template <class ST>
-__global__ void decode_kernel(const void* in, const float* scale, double* out, const double* vel64, int64_t K,
-                              int Np, int Q, int Qp) {
+__global__ void decode_kernel(const void* in, const float* scale, double* out, const double* vel64,
+                              const int32_t* iperm, int64_t K, int Np, int Q, int Qp) {
   using S = typename ST::S;
   const int64_t n = K * Np * Q;
   const double* w = vel64 + 2 * Qp;
   for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < n;
        idx += int64_t(gridDim.x) * blockDim.x) {
-    const int i = int(idx % Q);
+    const int i = iperm[int(idx % Q)];
     const int64_t kn = idx / Q;
     const int64_t k = kn / Np;
     const double s = ST::dev ? double(scale[k]) : 0.0;
@@ -193,11 +195,12 @@ __global__ void decode_kernel(const void* in, const float* scale, double* out, c
 }
 
 template <typename R>
-__global__ void decode_residual_kernel(const R* in, double* out, int64_t K, int Np, int Q, int Qp) {
+__global__ void decode_residual_kernel(const R* in, const int32_t* iperm, double* out, int64_t K, int Np, int Q,
+                                       int Qp) {
   const int64_t n = K * Np * Q;
   for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < n;
        idx += int64_t(gridDim.x) * blockDim.x) {
-    const int i = int(idx % Q);
+    const int i = iperm[int(idx % Q)];
     const int64_t kn = idx / Q;
     out[idx] = double(in[kn * Qp + i]);
   }
@@ -411,6 +414,7 @@ struct Group {
   void* geo = nullptr;          // [K][16] compute precision
   void* vel = nullptr;          // [kVelRows][Qp]
   double* vel64 = nullptr;      // [3][Qp]
+  int32_t* iperm = nullptr;     // [Q] internal index of canonical velocity c
   void* wall_feq = nullptr;     // [4 * ncases][Qp]
   void* wall_den_inv = nullptr; // [4 * ncases]
   double* Jk = nullptr;         // [K]
@@ -919,10 +923,43 @@ double relaxation_time(double kn, double L, int model) {
   }
 }
 
+// Internal velocity order: by direction (half-plane, then the sign of the
+// cross product), then speed, so that the 32 velocities of a warp point into a
+// narrow range of directions and mostly leave or enter an element through the
+// same faces (the warp-specialised kernel skips faces with no inflow for a
+// whole warp).  Exact comparisons of IEEE products: the same order on every
+// host.  order[j] = canonical index of internal velocity j.
+std::vector<int> direction_order(const VelocitySet& vs) {
+  std::vector<int> order(vs.Q);
+  for (int i = 0; i < vs.Q; ++i) order[i] = i;
+  auto half = [&](int i) { return vs.ey[i] < 0 || (vs.ey[i] == 0 && vs.ex[i] < 0) ? 1 : 0; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ha = half(a), hb = half(b);
+    if (ha != hb) return ha < hb;
+    const double cr = vs.ex[a] * vs.ey[b] - vs.ey[a] * vs.ex[b];
+    if (cr != 0) return cr > 0;
+    return vs.ex[a] * vs.ex[a] + vs.ey[a] * vs.ey[a] < vs.ex[b] * vs.ex[b] + vs.ey[b] * vs.ey[b];
+  });
+  return order;
+}
+
 // Host set-up of a group in FP64 (meshes, walls, geometry) and device upload.
 int build_group(Batch& b, Group& g) {
   std::string err;
   if (!build_velocity_set(g.vd, g.vs, err)) return fail(FEDBM_EINVAL, err);
+  // the device tables, state and residual hold the velocities in the internal
+  // order; set/get state and residual map the canonical order through iperm
+  const std::vector<int> order = direction_order(g.vs);
+  std::vector<int32_t> iperm(g.vs.Q);
+  {
+    VelocitySet canon = g.vs;
+    for (int j = 0; j < g.vs.Q; ++j) {
+      g.vs.ex[j] = canon.ex[order[j]];
+      g.vs.ey[j] = canon.ey[order[j]];
+      g.vs.w[j] = canon.w[order[j]];
+      iperm[order[j]] = j;
+    }
+  }
   if (!build_ref_ops(g.p, g.ops, err)) return fail(FEDBM_EINVAL, err);
   g.Np = g.ops.Np;
   g.Nfp = g.ops.Nfp;
@@ -1010,6 +1047,7 @@ int build_group(Batch& b, Group& g) {
   int rc;
   if ((rc = upload_vec(nbr, reinterpret_cast<void**>(&g.nbr))) != FEDBM_OK) return rc;
   if ((rc = upload_vec(v64, reinterpret_cast<void**>(&g.vel64))) != FEDBM_OK) return rc;
+  if ((rc = upload_vec(iperm, reinterpret_cast<void**>(&g.iperm))) != FEDBM_OK) return rc;
   if ((rc = upload_vec(Jk, reinterpret_cast<void**>(&g.Jk))) != FEDBM_OK) return rc;
   if ((rc = upload_vec(mw, reinterpret_cast<void**>(&g.mw))) != FEDBM_OK) return rc;
   if (g.store == kStoreF64) {
@@ -1047,8 +1085,8 @@ void free_batch(Batch* b) {
       cudaFree(g.f[c]);
       cudaFree(g.scale[c]);
     }
-    void* bufs[] = {g.res, g.nbr, g.geo, g.vel, g.vel64, g.wall_feq, g.wall_den_inv, g.Jk, g.mw, g.partial, g.flag,
-                    g.sr_step};
+    void* bufs[] = {g.res, g.nbr, g.geo, g.vel, g.vel64, g.iperm, g.wall_feq, g.wall_den_inv, g.Jk, g.mw, g.partial,
+                    g.flag, g.sr_step};
     for (void* p : bufs) cudaFree(p);
     if (g.branch) cudaStreamDestroy(g.branch);
   }
@@ -1192,10 +1230,10 @@ int encode_case(Batch& b, int c, const TIn* src) {
   float* sc = g.scale[b.cur] ? g.scale[b.cur] + cs.k_off : nullptr;
   const int blk = 256;
   switch (g.store) {
-    case kStoreF64: encode_kernel<StoreF64, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<double*>(g.f[b.cur]) + off, nullptr, g.vel64, g.Np, g.Q, g.Qp); break;
-    case kStoreF32: encode_kernel<StoreF32, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<float*>(g.f[b.cur]) + off, nullptr, g.vel64, g.Np, g.Q, g.Qp); break;
-    case kStoreBF16: encode_kernel<StoreBF16, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__nv_bfloat16*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
-    default: encode_kernel<StoreF16, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__half*>(g.f[b.cur]) + off, sc, g.vel64, g.Np, g.Q, g.Qp); break;
+    case kStoreF64: encode_kernel<StoreF64, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<double*>(g.f[b.cur]) + off, nullptr, g.vel64, g.iperm, g.Np, g.Q, g.Qp); break;
+    case kStoreF32: encode_kernel<StoreF32, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<float*>(g.f[b.cur]) + off, nullptr, g.vel64, g.iperm, g.Np, g.Q, g.Qp); break;
+    case kStoreBF16: encode_kernel<StoreBF16, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__nv_bfloat16*>(g.f[b.cur]) + off, sc, g.vel64, g.iperm, g.Np, g.Q, g.Qp); break;
+    default: encode_kernel<StoreF16, TIn><<<int(cs.K), blk, 0, b.stream>>>(src, static_cast<__half*>(g.f[b.cur]) + off, sc, g.vel64, g.iperm, g.Np, g.Q, g.Qp); break;
   }
   FEDBM_CK(cudaGetLastError());
   // a new state starts with a clear stage-kernel timeout word (and the
@@ -1234,7 +1272,7 @@ int set_equilibrium(Batch& b, int c, double rho0, double ux0, double uy0, double
   const int64_t n = cs.K * g.Np * g.Q;
   int rc = ensure_staging(b, size_t(n));
   if (rc) return rc;
-  equilibrium_kernel<<<grid_for(n, 256), 256, 0, b.stream>>>(b.staging, g.vel64, cs.K, g.Np, g.Q, g.Qp, rho0, ux0, uy0,
+  equilibrium_kernel<<<grid_for(n, 256), 256, 0, b.stream>>>(b.staging, g.vel64, g.iperm, cs.K, g.Np, g.Q, g.Qp, rho0, ux0, uy0,
                                                              amp, seed, g.vd.eq_order);
   FEDBM_CK(cudaGetLastError());
   return encode_case(b, c, static_cast<const double*>(b.staging));
@@ -1246,7 +1284,7 @@ void launch_decode(const Group& g, int cur, const Case& cs, double* dst, cudaStr
   const int64_t n = cs.K * g.Np * g.Q;
   const S* in = static_cast<const S*>(g.f[cur]) + size_t(cs.k_off) * g.Np * g.Qp;
   const float* sc = g.scale[cur] ? g.scale[cur] + cs.k_off : nullptr;
-  decode_kernel<ST><<<grid_for(n, 256), 256, 0, st>>>(in, sc, dst, g.vel64, cs.K, g.Np, g.Q, g.Qp);
+  decode_kernel<ST><<<grid_for(n, 256), 256, 0, st>>>(in, sc, dst, g.vel64, g.iperm, cs.K, g.Np, g.Q, g.Qp);
 }
 
 int get_state(Batch& b, int c, double* f, int on_device) {
@@ -1292,9 +1330,9 @@ int get_residual(Batch& b, int c, double* r, int on_device) {
   }
   const size_t off = size_t(cs.k_off) * g.Np * g.Qp;
   if (g.store == kStoreF64)
-    decode_residual_kernel<double><<<grid_for(n, 256), 256, 0, b.stream>>>(static_cast<const double*>(g.res) + off, dst, cs.K, g.Np, g.Q, g.Qp);
+    decode_residual_kernel<double><<<grid_for(n, 256), 256, 0, b.stream>>>(static_cast<const double*>(g.res) + off, g.iperm, dst, cs.K, g.Np, g.Q, g.Qp);
   else
-    decode_residual_kernel<float><<<grid_for(n, 256), 256, 0, b.stream>>>(static_cast<const float*>(g.res) + off, dst, cs.K, g.Np, g.Q, g.Qp);
+    decode_residual_kernel<float><<<grid_for(n, 256), 256, 0, b.stream>>>(static_cast<const float*>(g.res) + off, g.iperm, dst, cs.K, g.Np, g.Q, g.Qp);
   FEDBM_CK(cudaGetLastError());
   if (!on_device) {
     FEDBM_CK(cudaMemcpyAsync(r, dst, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, b.stream));
