@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 from oracle import couette, dg, ops, velset
+from tests import test_oracle_cavity_symmetry as tsym
 from tests import test_oracle_dg as tdg
 from tests import test_oracle_ops as tops
 from tests import test_oracle_velset as tvs
@@ -61,6 +62,7 @@ GH = lambda: (tvs.test_table1_d1q4_d1q5_closed_forms(), tvs.test_table1_d1q6_pri
               [tvs.test_gh_exact_to_degree_2n_minus_1(n) for n in (3, 4, 6)])
 NC = lambda: [tvs.test_nc_even_moments_corrected(n, s) for n, s in ((16, 1.0), (33, np.sqrt(2.0)))]
 COUETTE = tdg.test_couette_closed_form_matches_linearized_solve_and_tau_reading
+SYM = tsym.pins
 
 MUTATIONS = {
     # numerical flux (Sec. II.B.1): upwind weight with the wrong sign
@@ -81,6 +83,13 @@ MUTATIONS = {
     # volume term with the wrong sign
     "volume_sign": (RHS, "out = -(ar[:, None, :] * fr + as_[:, None, :] * fs)",
                     "out = (ar[:, None, :] * fr + as_[:, None, :] * fs)", [P0_FV, ENERGY]),
+    # metric term of the volume derivative taken from the wrong axis
+    "metric_sx_for_ry": (RHS, 'ey[None, :] * g["ry"][elems, None]', 'ey[None, :] * g["sx"][elems, None]',
+                         [SYM, ENERGY]),
+    # wall velocity components exchanged in the wall equilibrium (a moving lid
+    # then pushes along its normal instead of along the wall)
+    "lid_velocity_components_swapped": ((dg, dg.Problem, "_wall_states"), "equilibrium(1.0, u[0], u[1]",
+                                        "equilibrium(1.0, u[1], u[0]", [SYM]),
     # BGK term with the wrong sign, or multiplied by tau
     "collision_sign": (RHS, "out -= (fe - feq) / self.tau", "out += (fe - feq) / self.tau", [P0_FV]),
     "collision_times_tau": (RHS, "out -= (fe - feq) / self.tau", "out -= (fe - feq) * self.tau", [P0_FV]),
@@ -146,5 +155,5 @@ def test_lsrk_coefficient_typo_is_caught(monkeypatch):
 def test_unmutated_pins_pass():
     # the same pin groups pass on the oracle as committed
     groups = [P0_FV, ENERGY, FREE, REST, WALL_MASS, CONSERVE, LOW_MACH, TAU, LSRK, DERIV, MASSM, FACEM,
-              GEOM, GH, NC, COUETTE]
+              GEOM, GH, NC, COUETTE, SYM]
     assert _caught(groups) == 0
