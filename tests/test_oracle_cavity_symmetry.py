@@ -1,4 +1,5 @@
-"""The oracle's lid-driven cavity pinned by the symmetries of the square.
+"""The oracle's lid-driven cavity (and Couette flow) pinned by the symmetries
+of the square.
 
 The cavity of Sec. III.B has no closed-form solution, but the discrete method
 of Sec. II.B commutes with every isometry of the square that maps the mesh to
@@ -16,7 +17,10 @@ rounding.  Two isometries are used:
   split-square mesh becomes one whose diagonals run the other way (handed to
   the oracle as a triangle list);
 * the reflection across the diagonal y = x: the lid moves from y = 1 to
-  x = 1 with velocity (0, U), and the split-square mesh maps to itself.
+  x = 1 with velocity (0, U), and the split-square mesh maps to itself;
+* for Couette flow (Sec. III.A), the rotation by pi about the centre: the
+  plates change places with their velocities reversed, which is the same
+  problem, and the periodic seam maps onto itself.
 
 A mistake that treats x and y, or the two orientations of a face, unequally --
 a wrong metric term, a lid-velocity component taken from the wrong axis, a
@@ -45,20 +49,23 @@ def square_triangles(n):
     return vert, np.array(tri)
 
 
-def image_problem(pr, mesh, A, b, wall_u, **kw):
-    """The problem on the image of `mesh` under x -> A x + b, with every wall
-    velocity mapped by A onto the image of its side; triangles of a reflected
-    mesh are reversed so that they stay counter-clockwise."""
+def image_problem(pr, mesh, A, b, wall_u, bc=CAV, **kw):
+    """The problem on the image of `mesh` under x -> A x + b, with every side's
+    kind and wall velocity mapped (by A) onto the image of the side; triangles
+    of a reflected mesh are reversed so that they stay counter-clockwise."""
     vert, tri = mesh
     vert2 = vert @ A.T + b
     tri2 = tri[:, ::-1].copy() if np.linalg.det(A) < 0 else tri.copy()
     wall2 = np.zeros((4, 2))
+    bc2 = [None] * 4
     for s in range(4):
         n2 = A @ dg.SIDE_NORMAL[s]
         s2 = int(np.argmin(np.abs(dg.SIDE_NORMAL - n2).sum(axis=1)))
         assert np.allclose(dg.SIDE_NORMAL[s2], n2)
         wall2[s2] = A @ np.asarray(wall_u[s], dtype=float)
-    return dg.Problem(0, 0, pr.p, bc=CAV, wall_u=tuple(map(tuple, wall2)), mesh=(vert2, tri2), dt=pr.dt, **kw)
+        bc2[s2] = bc[s]
+    return dg.Problem(0, 0, pr.p, bc=tuple(bc2), wall_u=tuple(map(tuple, wall2)), mesh=(vert2, tri2),
+                      dt=pr.dt, **kw)
 
 
 def velocity_image(pr, A):
@@ -87,14 +94,22 @@ def node_image(pr, pr2, A, b):
 
 MIRROR_X = (np.array([[-1.0, 0.0], [0.0, 1.0]]), np.array([1.0, 0.0]))
 DIAGONAL = (np.array([[0.0, 1.0], [1.0, 0.0]]), np.array([0.0, 0.0]))
+ROTATE_PI = (np.array([[-1.0, 0.0], [0.0, -1.0]]), np.array([1.0, 1.0]))
+COUETTE_BC = ("diffuse", "periodic", "diffuse", "periodic")
 
 
-def check_isometry(A, b, p=2, velset=("gh", 4), eq_order=2, kn=1.0, lid=0.1, n=3, nsteps=2):
+def check_isometry(A, b, p=2, velset=("gh", 4), eq_order=2, kn=1.0, lid=0.1, n=3, nsteps=2, couette=False):
+    """Relative max difference between the original run and the image of the
+    image run.  The cavity has its lid (lid, 0) at y = 1; the Couette case
+    (periodic in x) has walls (-lid, 0) at y = 0 and (lid, 0) at y = 1."""
     mesh = square_triangles(n)
-    wall_u = ((0.0, 0.0), (0.0, 0.0), (lid, 0.0), (0.0, 0.0))
+    if couette:
+        bc, wall_u = COUETTE_BC, ((-lid, 0.0), (0.0, 0.0), (lid, 0.0), (0.0, 0.0))
+    else:
+        bc, wall_u = CAV, ((0.0, 0.0), (0.0, 0.0), (lid, 0.0), (0.0, 0.0))
     kw = dict(velset=velset, eq_order=eq_order, kn=kn)
-    pr = dg.Problem(0, 0, p, bc=CAV, wall_u=wall_u, mesh=mesh, **kw)
-    pr2 = image_problem(pr, mesh, A, b, wall_u, **kw)
+    pr = dg.Problem(0, 0, p, bc=bc, wall_u=wall_u, mesh=mesh, **kw)
+    pr2 = image_problem(pr, mesh, A, b, wall_u, bc=bc, **kw)
     j = velocity_image(pr, A)
     n2 = node_image(pr, pr2, A, b)
     kk = np.arange(pr.K)[:, None, None]
@@ -116,6 +131,14 @@ def test_cavity_commutes_with_square_isometries(iso, p, velset, eq_order):
     assert check_isometry(A, b, p=p, velset=velset, eq_order=eq_order) < 1e-13
 
 
+@pytest.mark.parametrize("p,velset", [(2, ("gh", 4)), (3, ("nc", 6))])
+def test_couette_commutes_with_rotation_by_pi(p, velset):
+    # the point reflection about the centre maps the plates onto each other
+    # with their velocities reversed, i.e. the Couette problem onto itself,
+    # and carries the periodic seam x = 0 ~ x = 1 onto itself
+    assert check_isometry(*ROTATE_PI, p=p, velset=velset, couette=True, n=4) < 1e-13
+
+
 def test_diagonal_reflection_maps_the_split_square_mesh_to_itself():
     # the element set of the image mesh is the original one (permuted), so the
     # diagonal check runs the cavity on the very mesh of the benchmark cases
@@ -129,3 +152,4 @@ def pins():
     """The pins as one call, for the planted-mistake tests."""
     for iso in (MIRROR_X, DIAGONAL):
         assert check_isometry(*iso) < 1e-13
+    assert check_isometry(*ROTATE_PI, couette=True, n=4) < 1e-13
